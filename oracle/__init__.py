@@ -1,0 +1,216 @@
+"""FP64 CPU oracle (test infrastructure only).
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may use this
+package.  It wraps the plain C implementation in xs_oracle.c through ctypes; the
+C file is compiled here with gcc (OpenMP) on first use or by build().
+It shares no code with the CUDA library in paper_2105_14782_gb300/.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_d = C.c_double
+_i32 = C.c_int32
+_i64 = C.c_int64
+_pd = C.POINTER(C.c_double)
+
+
+def build(force: bool = False) -> str:
+    """Compile xs_oracle.c into liboracle.so (gcc -O2 -fopenmp, no fast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC, "-o", tmp, "-lm"],
+                       check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = C.CDLL(_LIB)
+            lib.orc_num_threads.restype = C.c_int
+            lib.orc_faddeeva_v.argtypes = [_i64, _pd, _pd, _pd, _pd]
+            lib.orc_line_params.argtypes = [_i64, _pd, _pd, _pd, _pd, _pd, _d, _d, _d, _d, _d, _pd, _pd, _pd]
+            lib.orc_xs.argtypes = [_i64, _pd, _pd, _pd, _pd, _pd, _d, _d, _i64, _pd, _i32, _pd, _pd, _d, _d, _pd]
+            lib.orc_xs_points.argtypes = [_i64, _pd, _pd, _pd, _pd, _pd, _d, _d, _pd, _i32, _pd, _pd, _d, _d,
+                                          _i64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), _pd]
+            lib.orc_tau.argtypes = [_i32, C.POINTER(_pd), _pd, _pd, _pd, _i32, _i64, _d, _d, _d, _pd]
+            for f in ("orc_e1", "orc_e2", "orc_e3", "orc_trans"):
+                getattr(lib, f).argtypes = [_d]
+                getattr(lib, f).restype = _d
+            lib.orc_trans_v.argtypes = [_i64, _pd, _pd]
+            lib.orc_planck_pi.argtypes = [_d, _d]
+            lib.orc_planck_pi.restype = _d
+            lib.orc_emission.argtypes = [_pd, _pd, _pd, _i32, _i64, _pd]
+            lib.orc_emission_recurrence.argtypes = [_pd, _pd, _pd, _i32, _i64, _pd]
+            lib.orc_loglike.argtypes = [_pd, _pd, _pd, _i64]
+            lib.orc_loglike.restype = _d
+            lib.orc_logl_grad.argtypes = [_i32, C.POINTER(C.c_int64), _pd, _pd, _pd, _pd, _pd, _pd, _pd, _i64,
+                                          _pd, _i32, _pd, _pd, _d, _d, _d, _d, _pd, _pd, _pd, _pd, _pd]
+            lib.orc_logl_grad.restype = _d
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(_pd)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+def faddeeva(x, a):
+    """w(x + i a) for a >= 0, elementwise; returns complex128."""
+    x = _f64(x).ravel()
+    a = _f64(np.broadcast_to(a, x.shape)).ravel()
+    re = np.empty_like(x)
+    im = np.empty_like(x)
+    _load().orc_faddeeva_v(x.size, _p(x), _p(a), _p(re), _p(im))
+    return re + 1j * im
+
+
+def line_params(lines, T, P_bar, sb=1.0):
+    """(S(T), beta, gamma) per line, input order."""
+    arr = [_f64(v) for v in lines.arrays()]
+    n = arr[0].size
+    S, b, g = np.empty(n), np.empty(n), np.empty(n)
+    _load().orc_line_params(n, *[_p(v) for v in arr], lines.mass_amu, lines.q_exponent, float(T), float(P_bar),
+                            float(sb), _p(S), _p(b), _p(g))
+    return S, b, g
+
+
+def xs(lines, nu, T, P_bar, sb=1.0, wing_cut=25.0):
+    """sigma[L][N] (cm^2/molecule) for one species."""
+    arr = [_f64(v) for v in lines.arrays()]
+    nu = _f64(nu)
+    T = _f64(np.atleast_1d(T))
+    P = _f64(np.atleast_1d(P_bar))
+    out = np.empty((T.size, nu.size))
+    _load().orc_xs(arr[0].size, *[_p(v) for v in arr], lines.mass_amu, lines.q_exponent, nu.size, _p(nu),
+                   T.size, _p(T), _p(P), float(sb), float(wing_cut), _p(out))
+    return out
+
+
+def xs_points(lines, nu, T, P_bar, layer_idx, grid_idx, sb=1.0, wing_cut=25.0):
+    """sigma at the given (layer, grid index) pairs."""
+    arr = [_f64(v) for v in lines.arrays()]
+    nu = _f64(nu)
+    T = _f64(np.atleast_1d(T))
+    P = _f64(np.atleast_1d(P_bar))
+    li = np.ascontiguousarray(layer_idx, dtype=np.int32)
+    gi = np.ascontiguousarray(grid_idx, dtype=np.int64)
+    out = np.empty(li.size)
+    _load().orc_xs_points(arr[0].size, *[_p(v) for v in arr], lines.mass_amu, lines.q_exponent, _p(nu), T.size,
+                          _p(T), _p(P), float(sb), float(wing_cut), li.size,
+                          li.ctypes.data_as(C.POINTER(C.c_int32)), gi.ctypes.data_as(C.POINTER(C.c_int64)),
+                          _p(out))
+    return out
+
+
+def tau(sigmas, vmr, P_bar, dP_bar, g=1e5, mu=2.313, kappa_coef=1e-8):
+    """dtau[L][N] from per-species sigma[L][N] and vmr[S][L]."""
+    sig = [_f64(s) for s in sigmas]
+    L, N = sig[0].shape
+    vm = _f64(np.broadcast_to(np.asarray(vmr, dtype=np.float64).reshape(len(sig), -1), (len(sig), L)))
+    P, dP = _f64(P_bar), _f64(dP_bar)
+    ptrs = (_pd * len(sig))(*[_p(s) for s in sig])
+    out = np.empty((L, N))
+    _load().orc_tau(len(sig), ptrs, _p(vm), _p(P), _p(dP), L, N, g, mu, kappa_coef, _p(out))
+    return out
+
+
+def e1(x):
+    return _load().orc_e1(float(x))
+
+
+def e2(x):
+    return _load().orc_e2(float(x))
+
+
+def e3(x):
+    return _load().orc_e3(float(x))
+
+
+def trans(x):
+    x = _f64(np.atleast_1d(x)).ravel()
+    out = np.empty_like(x)
+    _load().orc_trans_v(x.size, _p(x), _p(out))
+    return out
+
+
+def planck_pi(nu, T):
+    return _load().orc_planck_pi(float(nu), float(T))
+
+
+def emission(dtau, T, nu):
+    dtau, T, nu = _f64(dtau), _f64(T), _f64(nu)
+    L, N = dtau.shape
+    out = np.empty(N)
+    _load().orc_emission(_p(dtau), _p(T), _p(nu), L, N, _p(out))
+    return out
+
+
+def emission_recurrence(dtau, T, nu):
+    dtau, T, nu = _f64(dtau), _f64(T), _f64(nu)
+    L, N = dtau.shape
+    out = np.empty(N)
+    _load().orc_emission_recurrence(_p(dtau), _p(T), _p(nu), L, N, _p(out))
+    return out
+
+
+def loglike(F, d, sig):
+    F, d, sig = _f64(F), _f64(d), _f64(sig)
+    return _load().orc_loglike(_p(F), _p(d), _p(sig), F.size)
+
+
+def temperatures(T0, alpha, P_bar):
+    """T_n = T0 (P_n / 1 bar)^alpha (the power-law profile of Sec. 5.2)."""
+    return T0 * np.power(_f64(P_bar), alpha)
+
+
+def forward(atm, theta):
+    """F0[N] for theta = (T0, alpha, log10 xi_0..log10 xi_{S-1}, s_b)."""
+    S = len(atm.species)
+    T = temperatures(theta[0], theta[1], atm.p_bar)
+    sig = [xs(sp, atm.nu, T, atm.p_bar, sb=theta[2 + S], wing_cut=atm.wing_cut) for sp in atm.species]
+    vmr = np.array([[10.0 ** theta[2 + m]] * len(atm.p_bar) for m in range(S)])
+    dt = tau(sig, vmr, atm.p_bar, atm.dp_bar, atm.gravity, atm.mu, atm.kappa_coef)
+    return emission(dt, T, atm.nu)
+
+
+def logl_grad(atm, theta, dobs, sig_obs):
+    """(logL, dlogL/dtheta, F0) by forward-mode duals."""
+    S = len(atm.species)
+    nl = np.array([sp.n for sp in atm.species], dtype=np.int64)
+    cat = [_f64(np.concatenate([getattr(sp, f) for sp in atm.species]))
+           for f in ("nu_hat", "ln_S0", "elower", "gamma_ref", "n_temp")]
+    mass = _f64([sp.mass_amu for sp in atm.species])
+    qexp = _f64([sp.q_exponent for sp in atm.species])
+    nu, P, dP = _f64(atm.nu), _f64(atm.p_bar), _f64(atm.dp_bar)
+    th = _f64(theta)
+    d, s = _f64(dobs), _f64(sig_obs)
+    grad = np.zeros(3 + S)
+    F0 = np.empty(nu.size)
+    ll = _load().orc_logl_grad(S, nl.ctypes.data_as(C.POINTER(C.c_int64)), *[_p(v) for v in cat], _p(mass),
+                               _p(qexp), nu.size, _p(nu), P.size, _p(P), _p(dP), atm.gravity, atm.mu,
+                               atm.kappa_coef, atm.wing_cut, _p(th), _p(d), _p(s), _p(grad), _p(F0))
+    return ll, grad, F0
