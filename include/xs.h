@@ -1,0 +1,227 @@
+/*
+ * libxs — C ABI of the GB300 (sm_103a) line-by-line opacity, optical-depth and
+ * emission library for the auto-differentiable spectrum model of Kawahara et al.
+ * (arXiv:2105.14782).
+ *
+ * Conventions shared by every entry point:
+ *   - Every array argument is a DEVICE pointer unless it is marked "host".
+ *     The caller owns all memory; the library never allocates device memory.
+ *     Scratch comes from a caller-provided workspace whose size the matching
+ *     *_workspace_bytes() function returns (a 256-byte aligned device buffer).
+ *   - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *     stream).  Results are valid once the stream reaches that point.
+ *   - Layouts are row-major: [L][N] means layer-major, grid index fastest.
+ *     Layer 0 is the top of the atmosphere (lowest pressure).
+ *   - Units: wavenumber cm^-1, pressure bar, temperature K, cross-section
+ *     cm^2/molecule, flux erg s^-1 cm^-2 (cm^-1)^-1 (cgs).
+ *   - Return value: XS_OK or a negative xs_status.  Argument errors are detected
+ *     on the host before any launch and leave outputs untouched; XS_ECUDA reports
+ *     a launch or runtime error (cudaGetLastError).  Nothing is printed and no
+ *     entry point aborts the process.
+ */
+#ifndef XS_H
+#define XS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* xs_stream; /* same object as cudaStream_t */
+
+typedef enum {
+    XS_OK = 0,
+    XS_EINVAL = -1,    /* null pointer, non-positive size, bad precision, too small workspace */
+    XS_EUNSORTED = -2, /* line centres not ascending, or grid not strictly increasing */
+    XS_ENOMEM = -3,    /* reserved for host-side allocation failure */
+    XS_ECUDA = -4,     /* a CUDA launch or runtime call failed */
+    XS_ETIMEOUT = -5   /* a bounded host-side wait ran out */
+} xs_status;
+
+typedef enum {
+    XS_PREC_FP64 = 0, /* every step in double precision */
+    XS_PREC_MIXED = 1 /* Voigt evaluation and line sum in FP32 (compensated), line-centre
+                         offsets and strength exponentials in FP64; sigma stored as float */
+} xs_prec;
+
+#define XS_MAX_SPECIES 8
+
+/*
+ * One species' line list, structure of arrays, device memory, sorted by nu_hat
+ * ascending (xs_sort_lines_host sorts host copies; xs_check_sorted verifies).
+ * Fields follow the HITRAN-style parameter table of Sec. 2.2 (Table 1).
+ */
+typedef struct {
+    int64_t n;               /* number of lines (0 allowed) */
+    const double* nu_hat;    /* [n] line centre, cm^-1 */
+    const double* ln_S0;     /* [n] ln of the line strength at T_ref = 296 K, ln(cm/molecule) */
+    const double* elower;    /* [n] lower-state energy E'', cm^-1 */
+    const double* gamma_ref; /* [n] Lorentz HWHM at 296 K and 1 atm, cm^-1 atm^-1 */
+    const double* n_temp;    /* [n] temperature exponent of the width */
+    double mass_amu;         /* molecular mass M in atomic mass units */
+    double q_exponent;       /* partition-function ratio Q(T)/Q(296) = (T/296)^q_exponent */
+} xs_lines;
+
+/* Human-readable name of a status code (static string). */
+const char* xs_strerror(int status);
+
+/*
+ * Stable in-place sort of a HOST line list by centre (ties keep input order).
+ * All five arrays are permuted together.  Line-list ingest step; Table 1 fields.
+ * Returns XS_EINVAL on null arrays with n > 0.
+ */
+int xs_sort_lines_host(int64_t n, double* nu_hat, double* ln_S0, double* elower, double* gamma_ref,
+                       double* n_temp);
+
+/*
+ * Synchronously checks the order of a device array v[n]: non-decreasing when
+ * strict == 0 (line centres), strictly increasing when strict != 0 (a grid).
+ * flag_dev is one caller-owned device int used as scratch.  Returns XS_OK,
+ * XS_EUNSORTED or XS_ECUDA; blocks the calling thread until `stream` drains.
+ */
+int xs_check_sorted(const double* v, int64_t n, int strict, int* flag_dev, xs_stream stream);
+
+/* Workspace bytes xs_compute / xs_compute_adjoint need for these sizes.  A
+ * workspace down to xs_workspace_min_bytes still works (layers are then done in
+ * chunks); sizes in between pick the largest chunk that fits. */
+size_t xs_workspace_bytes(int64_t n_lines, int64_t N, int32_t L, int prec);
+size_t xs_workspace_min_bytes(int64_t n_lines, int64_t N, int32_t L, int prec);
+
+/*
+ * Cross-section of one species on a grid for every layer (Eq. crosssec, the
+ * direct line-profile sum of Sec. 2.1.1 and Sec. 3.1):
+ *   sigma[n][j] = sum over lines l with |nu[j] - nu_hat[l]| <= wing_cut of
+ *                 S_l(T_n) / (sqrt(2 pi) beta_l) * H(x, a),
+ *   x = (nu[j] - nu_hat[l]) / (sqrt(2) beta_l),  a = gamma_l / (sqrt(2) beta_l),
+ * with S(T) of Eq. Slog, beta of Eq. thermal, and
+ *   gamma_l = broad_scale * gamma_ref_l * (T_n/296)^(-n_temp_l) * (P_bar[n] / 1.01325)
+ * (Eq. gammahitran without the self and natural terms).  The wing-cut test is
+ * made in double precision and includes the boundary.
+ *   nu      [N] strictly increasing grid (any spacing), cm^-1
+ *   T,P_bar [L] layer temperature (K) and pressure (bar), device
+ *   sigma   [L][N] output: double for XS_PREC_FP64, float for XS_PREC_MIXED
+ * Lines must be sorted by centre.  n == 0 gives sigma = 0.
+ */
+int xs_compute(const xs_lines* lines, const double* nu, int64_t N, const double* T, const double* P_bar,
+               int32_t L, double broad_scale, double wing_cut, int prec, void* sigma, void* workspace,
+               size_t workspace_bytes, xs_stream stream);
+
+/*
+ * Reverse-mode adjoint of xs_compute.  Given g_sigma[n][j] = dF/dsigma[n][j]
+ * (double, [L][N]) it writes
+ *   g_T[n]     = sum_j g_sigma[n][j] d sigma[n][j] / d T_n        (through S, beta, gamma)
+ *   g_broad[0] = sum_{n,j} g_sigma[n][j] d sigma[n][j] / d broad_scale
+ * Voigt values are recomputed, not stored; dH/dx and dH/da follow the
+ * relations of Sec. 2.1.1 (dH/dx = 2aL - 2xH, dH/da = 2xL + 2aH - 2/sqrt(pi)).
+ * The reduction order is fixed, so repeated calls give identical bits.
+ * g_T [L] and g_broad [1] are overwritten (double, device).
+ */
+int xs_compute_adjoint(const xs_lines* lines, const double* nu, int64_t N, const double* T,
+                       const double* P_bar, int32_t L, double broad_scale, double wing_cut, int prec,
+                       const double* g_sigma, double* g_T, double* g_broad, void* workspace,
+                       size_t workspace_bytes, xs_stream stream);
+
+/*
+ * Layer optical depth (Eq. dtau_line) plus a grey continuum:
+ *   dtau[n][j] = dP_n 1e6 / (mu m_u g) * sum_m vmr[m][n] sigma_m[n][j]
+ *              + kappa_coef * P_n * dP_n * 1e6 / g
+ * sigma: HOST array of S device pointers, each [L][N] (double for FP64, float
+ * for MIXED).  vmr [S][L] device.  P_bar, dP_bar [L] device (bar).  g in
+ * cm s^-2, mu the mean molecular weight.  dtau [L][N] double output.
+ */
+int tau_layers(const void* const* sigma, int32_t S, const double* vmr, const double* P_bar,
+               const double* dP_bar, int32_t L, int64_t N, double gravity, double mu, double kappa_coef,
+               int prec, double* dtau, xs_stream stream);
+
+/*
+ * Adjoint of tau_layers: from g_dtau [L][N] writes g_sigma[m] = g_dtau * dP 1e6/(mu m_u g) * vmr[m][n]
+ * ([L][N] double each; `g_sigma` is a HOST array of S device pointers; a NULL
+ * entry skips that species) and g_vmr[m][n] = sum_j g_dtau[n][j] * dtau_m[n][j] / vmr[m][n]
+ * ([S][L] double), summed in a fixed order.
+ */
+int tau_layers_adjoint(const void* const* sigma, int32_t S, const double* vmr, const double* P_bar,
+                       const double* dP_bar, int32_t L, int64_t N, double gravity, double mu, int prec,
+                       const double* g_dtau, double* const* g_sigma, double* g_vmr, xs_stream stream);
+
+/*
+ * Top-of-atmosphere flux of the pure-absorption two-stream solve (Sec. 3):
+ *   F0[j] = sum_n Phi_n (1 - T_n) S_n + Phi_L F_B,  Phi_n = prod_{k<n} T_k,
+ *   T_n = 2 E3(dtau[n][j]) (Eq. trans), S_n = pi B(nu_j, T_n) (Eq. sourcepla),
+ *   F_B = pi B(nu_j, T_{L-1}) (opaque bottom at the deepest layer's temperature).
+ * dtau [L][N], T [L], nu [N] double in; F0 [N] double out.
+ */
+int emission_spectrum(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
+                      xs_stream stream);
+
+/* Workspace bytes emission_spectrum_adjoint needs. */
+size_t emission_workspace_bytes(int32_t L, int64_t N);
+
+/*
+ * Adjoint of emission_spectrum.  From g_F0 [N] writes g_dtau [L][N] (overwritten)
+ * and g_T [L] (overwritten: the Planck-source part of dF/dT_n only), using the
+ * layer recurrence F_n = T_n F_{n+1} + (1 - T_n) S_n (Eq. rerr) swept bottom-up
+ * and top-down; dT/d dtau = -2 E2(dtau).  Fixed reduction order.
+ */
+int emission_spectrum_adjoint(const double* g_F0, const double* dtau, const double* T, const double* nu,
+                              int32_t L, int64_t N, double* g_dtau, double* g_T, void* workspace,
+                              size_t workspace_bytes, xs_stream stream);
+
+/*
+ * Gaussian log-likelihood with fixed per-point errors (Eq. likelihood without
+ * the jitter term): logL = -1/2 sum_j ((d_j - F_j)/s_j)^2 written to logL[0];
+ * g_F[j] = (d_j - F_j)/s_j^2 if g_F is not NULL.  All device, double.
+ */
+int loglike_gauss(const double* F, const double* d, const double* s, int64_t N, double* logL, double* g_F,
+                  xs_stream stream);
+
+/*
+ * Power-law temperature profile of Sec. 5.2: T[n] = T0 * P_bar[n]^alpha (P in bar).
+ */
+int layer_temperatures(double T0, double alpha, const double* P_bar, int32_t L, double* T, xs_stream stream);
+
+/*
+ * A whole emission model: species line lists, grid, layers, observed spectrum.
+ * All pointers device.  Used by the composite calls below.
+ */
+typedef struct {
+    int32_t n_species;
+    xs_lines species[XS_MAX_SPECIES];
+    const double* nu; /* [N] */
+    int64_t N;
+    const double* P_bar;  /* [L] */
+    const double* dP_bar; /* [L] */
+    int32_t L;
+    double wing_cut;
+    double gravity;
+    double mu;
+    double kappa_coef;
+    const double* d_obs;   /* [N] observed spectrum (may be NULL for forward-only use) */
+    const double* sig_obs; /* [N] its 1-sigma errors */
+    int prec;
+} xs_model;
+
+size_t xs_model_workspace_bytes(const xs_model* model);
+
+/*
+ * Forward model for theta = (T0, alpha, log10 vmr_0 .. log10 vmr_{S-1}, broad_scale)
+ * (HOST array of 3 + S doubles): layer temperatures (Sec. 5.2 power law), every
+ * species' cross-section, optical depth and emission.  F0 [N] device output.
+ */
+int xs_model_forward(const xs_model* model, const double* theta, double* F0, void* workspace,
+                     size_t workspace_bytes, xs_stream stream);
+
+/*
+ * Forward model plus the log-likelihood and its gradient by the hand-written
+ * adjoints (reverse mode).  out [1 + 3 + S] device doubles: logL, then dlogL/dtheta
+ * in theta's order.  F0 [N] is written when not NULL.
+ */
+int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, double* F0, void* workspace,
+                       size_t workspace_bytes, xs_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XS_H */

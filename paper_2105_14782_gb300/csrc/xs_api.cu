@@ -1,0 +1,313 @@
+// C ABI of libxs: argument checks, workspace plans and the composite model
+// calls.  Every entry point returns an xs_status and never throws or prints.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "xs_internal.h"
+
+namespace {
+
+inline cudaStream_t S(xs_stream s) { return (cudaStream_t)s; }
+inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
+inline bool prec_ok(int p) { return p == XS_PREC_FP64 || p == XS_PREC_MIXED; }
+
+int check_lines(const xs_lines* ln)
+{
+    if (!ln || ln->n < 0) return XS_EINVAL;
+    if (ln->n > 0 && (!ln->nu_hat || !ln->ln_S0 || !ln->elower || !ln->gamma_ref || !ln->n_temp)) return XS_EINVAL;
+    if (ln->n >= (int64_t)1 << 31) return XS_EINVAL;
+    if (!(ln->mass_amu > 0.0) || !std::isfinite(ln->q_exponent)) return XS_EINVAL;
+    return XS_OK;
+}
+
+int check_common(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L,
+                 double sb, double W, int prec)
+{
+    int r = check_lines(ln);
+    if (r) return r;
+    if (!nu || !T || !P || N <= 0 || L <= 0 || N >= ((int64_t)1 << 31) - 2048) return XS_EINVAL;
+    if (!(W > 0.0) || !(sb > 0.0) || !prec_ok(prec)) return XS_EINVAL;
+    return XS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+const char* xs_strerror(int status)
+{
+    switch (status) {
+    case XS_OK: return "ok";
+    case XS_EINVAL: return "invalid argument";
+    case XS_EUNSORTED: return "line centres or grid not in ascending order";
+    case XS_ENOMEM: return "out of host memory";
+    case XS_ECUDA: return "CUDA error";
+    case XS_ETIMEOUT: return "timed out";
+    default: return "unknown status";
+    }
+}
+
+int xs_sort_lines_host(int64_t n, double* nu_hat, double* ln_S0, double* elower, double* gamma_ref, double* n_temp)
+{
+    if (n < 0) return XS_EINVAL;
+    if (n == 0) return XS_OK;
+    if (!nu_hat || !ln_S0 || !elower || !gamma_ref || !n_temp) return XS_EINVAL;
+    std::vector<int64_t> idx((size_t)n);
+    std::iota(idx.begin(), idx.end(), (int64_t)0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) { return nu_hat[a] < nu_hat[b]; });
+    std::vector<double> tmp((size_t)n);
+    double* f[5] = {nu_hat, ln_S0, elower, gamma_ref, n_temp};
+    for (double* a : f) {
+        for (int64_t i = 0; i < n; ++i) tmp[(size_t)i] = a[idx[(size_t)i]];
+        std::memcpy(a, tmp.data(), sizeof(double) * (size_t)n);
+    }
+    return XS_OK;
+}
+
+int xs_check_sorted(const double* v, int64_t n, int strict, int* flag_dev, xs_stream stream)
+{
+    if (n < 0 || (n > 0 && !v) || !flag_dev) return XS_EINVAL;
+    return xsi::check_sorted(v, n, S(stream), flag_dev, strict != 0);
+}
+
+int xs_compute(const xs_lines* lines, const double* nu, int64_t N, const double* T, const double* P_bar, int32_t L,
+               double broad_scale, double wing_cut, int prec, void* sigma, void* workspace, size_t workspace_bytes,
+               xs_stream stream)
+{
+    int r = check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
+    if (r) return r;
+    if (!sigma || !workspace) return XS_EINVAL;
+    if (workspace_bytes < xs_workspace_min_bytes(lines->n, N, L, prec)) return XS_EINVAL;
+    return xsi::xs_run(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec, sigma, workspace, workspace_bytes,
+                       false, nullptr, nullptr, nullptr, S(stream));
+}
+
+int xs_compute_adjoint(const xs_lines* lines, const double* nu, int64_t N, const double* T, const double* P_bar,
+                       int32_t L, double broad_scale, double wing_cut, int prec, const double* g_sigma, double* g_T,
+                       double* g_broad, void* workspace, size_t workspace_bytes, xs_stream stream)
+{
+    int r = check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
+    if (r) return r;
+    if (!g_sigma || !g_T || !g_broad || !workspace) return XS_EINVAL;
+    if (workspace_bytes < xs_workspace_min_bytes(lines->n, N, L, prec)) return XS_EINVAL;
+    return xsi::xs_run(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec, nullptr, workspace, workspace_bytes,
+                       true, g_sigma, g_T, g_broad, S(stream));
+}
+
+int tau_layers(const void* const* sigma, int32_t nsp, const double* vmr, const double* P_bar, const double* dP_bar,
+               int32_t L, int64_t N, double gravity, double mu, double kappa_coef, int prec, double* dtau,
+               xs_stream stream)
+{
+    if (!sigma || nsp < 1 || nsp > XS_MAX_SPECIES || !vmr || !P_bar || !dP_bar || L <= 0 || N <= 0 || !dtau)
+        return XS_EINVAL;
+    for (int m = 0; m < nsp; ++m)
+        if (!sigma[m]) return XS_EINVAL;
+    if (!(gravity > 0.0) || !(mu > 0.0) || !prec_ok(prec) || !std::isfinite(kappa_coef)) return XS_EINVAL;
+    return xsi::rt_tau(sigma, nsp, vmr, P_bar, dP_bar, L, N, gravity, mu, kappa_coef, prec, dtau, S(stream));
+}
+
+int tau_layers_adjoint(const void* const* sigma, int32_t nsp, const double* vmr, const double* P_bar,
+                       const double* dP_bar, int32_t L, int64_t N, double gravity, double mu, int prec,
+                       const double* g_dtau, double* const* g_sigma, double* g_vmr, xs_stream stream)
+{
+    if (!sigma || nsp < 1 || nsp > XS_MAX_SPECIES || !vmr || !P_bar || !dP_bar || L <= 0 || N <= 0 || !g_dtau ||
+        !g_vmr)
+        return XS_EINVAL;
+    for (int m = 0; m < nsp; ++m)
+        if (!sigma[m]) return XS_EINVAL;
+    if (!(gravity > 0.0) || !(mu > 0.0) || !prec_ok(prec)) return XS_EINVAL;
+    return xsi::rt_tau_adjoint(sigma, nsp, vmr, P_bar, dP_bar, L, N, gravity, mu, prec, g_dtau, g_sigma, g_vmr,
+                               S(stream));
+}
+
+int emission_spectrum(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
+                      xs_stream stream)
+{
+    if (!dtau || !T || !nu || L <= 0 || N <= 0 || !F0) return XS_EINVAL;
+    return xsi::rt_emission(dtau, T, nu, L, N, F0, S(stream));
+}
+
+size_t emission_workspace_bytes(int32_t L, int64_t N)
+{
+    if (L <= 0 || N <= 0) return 0;
+    return al(xsi::rt_emission_ws(L, N));
+}
+
+int emission_spectrum_adjoint(const double* g_F0, const double* dtau, const double* T, const double* nu, int32_t L,
+                              int64_t N, double* g_dtau, double* g_T, void* workspace, size_t workspace_bytes,
+                              xs_stream stream)
+{
+    if (!g_F0 || !dtau || !T || !nu || L <= 0 || N <= 0 || !g_dtau || !g_T || !workspace) return XS_EINVAL;
+    if (workspace_bytes < emission_workspace_bytes(L, N)) return XS_EINVAL;
+    return xsi::rt_emission_adjoint(g_F0, dtau, T, nu, L, N, g_dtau, g_T, workspace, S(stream));
+}
+
+int loglike_gauss(const double* F, const double* d, const double* s, int64_t N, double* logL, double* g_F,
+                  xs_stream stream)
+{
+    if (!F || !d || !s || N <= 0 || !logL) return XS_EINVAL;
+    return xsi::rt_loglike(F, d, s, N, logL, g_F, S(stream));
+}
+
+int layer_temperatures(double T0, double alpha, const double* P_bar, int32_t L, double* T, xs_stream stream)
+{
+    if (!P_bar || !T || L <= 0 || !(T0 > 0.0) || !std::isfinite(alpha)) return XS_EINVAL;
+    return xsi::rt_temperatures(T0, alpha, P_bar, L, T, S(stream));
+}
+
+} // extern "C"
+
+// ------------------------------------------------------------ composite model
+
+namespace {
+
+struct ModelPlan {
+    size_t T, vmr, sigma, dtau, F0, gF, gdtau, gsig, gvmr, gT, gTtmp, gb, xsws, emws, total;
+    size_t xsws_bytes;
+    int64_t max_nl;
+};
+
+int check_model(const xs_model* m)
+{
+    if (!m || m->n_species < 1 || m->n_species > XS_MAX_SPECIES) return XS_EINVAL;
+    if (!m->nu || m->N <= 0 || !m->P_bar || !m->dP_bar || m->L <= 0) return XS_EINVAL;
+    if (!(m->wing_cut > 0.0) || !(m->gravity > 0.0) || !(m->mu > 0.0) || !prec_ok(m->prec)) return XS_EINVAL;
+    for (int s = 0; s < m->n_species; ++s)
+        if (check_lines(&m->species[s])) return XS_EINVAL;
+    return XS_OK;
+}
+
+ModelPlan plan_model(const xs_model* m)
+{
+    ModelPlan p{};
+    const int Sp = m->n_species;
+    const size_t LN = (size_t)m->L * (size_t)m->N;
+    const size_t es = (m->prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
+    p.max_nl = 0;
+    for (int s = 0; s < Sp; ++s) p.max_nl = std::max<int64_t>(p.max_nl, m->species[s].n);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += al(bytes);
+        return o;
+    };
+    p.T = take(sizeof(double) * m->L);
+    p.vmr = take(sizeof(double) * Sp * m->L);
+    p.sigma = take(es * LN * Sp);
+    p.dtau = take(sizeof(double) * LN);
+    p.F0 = take(sizeof(double) * m->N);
+    p.gF = take(sizeof(double) * m->N);
+    p.gdtau = take(sizeof(double) * LN);
+    p.gsig = take(sizeof(double) * LN * Sp);
+    p.gvmr = take(sizeof(double) * Sp * m->L);
+    p.gT = take(sizeof(double) * m->L);
+    p.gTtmp = take(sizeof(double) * m->L);
+    p.gb = take(sizeof(double) * Sp);
+    p.xsws_bytes = xs_workspace_bytes(p.max_nl, m->N, m->L, m->prec);
+    p.xsws = take(p.xsws_bytes);
+    p.emws = take(emission_workspace_bytes(m->L, m->N));
+    p.total = off;
+    return p;
+}
+
+int model_forward_impl(const xs_model* m, const double* theta, double* F0out, char* ws, const ModelPlan& p,
+                       cudaStream_t st)
+{
+    const int Sp = m->n_species;
+    const size_t LN = (size_t)m->L * (size_t)m->N;
+    const size_t es = (m->prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
+    double* T = (double*)(ws + p.T);
+    double* vmr = (double*)(ws + p.vmr);
+    char* sig = ws + p.sigma;
+    double* dtau = (double*)(ws + p.dtau);
+    int r = xsi::rt_temperatures(theta[0], theta[1], m->P_bar, m->L, T, st);
+    if (r) return r;
+    r = xsi::rt_fill_vmr(nullptr, Sp, m->L, theta + 2, vmr, st);
+    if (r) return r;
+    const void* sp[XS_MAX_SPECIES];
+    for (int s = 0; s < Sp; ++s) {
+        sp[s] = sig + es * LN * s;
+        r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec,
+                        (void*)sp[s], ws + p.xsws, p.xsws_bytes, false, nullptr, nullptr, nullptr, st);
+        if (r) return r;
+    }
+    r = xsi::rt_tau(sp, Sp, vmr, m->P_bar, m->dP_bar, m->L, m->N, m->gravity, m->mu, m->kappa_coef, m->prec, dtau, st);
+    if (r) return r;
+    return xsi::rt_emission(dtau, T, m->nu, m->L, m->N, F0out, st);
+}
+
+} // namespace
+
+extern "C" {
+
+size_t xs_model_workspace_bytes(const xs_model* model)
+{
+    if (check_model(model)) return 0;
+    return plan_model(model).total;
+}
+
+int xs_model_forward(const xs_model* model, const double* theta, double* F0, void* workspace, size_t workspace_bytes,
+                     xs_stream stream)
+{
+    int r = check_model(model);
+    if (r) return r;
+    if (!theta || !F0 || !workspace) return XS_EINVAL;
+    ModelPlan p = plan_model(model);
+    if (workspace_bytes < p.total) return XS_EINVAL;
+    if (!(theta[0] > 0.0) || !(theta[2 + model->n_species] > 0.0)) return XS_EINVAL;
+    return model_forward_impl(model, theta, F0, (char*)workspace, p, S(stream));
+}
+
+int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, double* F0, void* workspace,
+                       size_t workspace_bytes, xs_stream stream)
+{
+    int r = check_model(m);
+    if (r) return r;
+    if (!theta || !out || !workspace || !m->d_obs || !m->sig_obs) return XS_EINVAL;
+    ModelPlan p = plan_model(m);
+    if (workspace_bytes < p.total) return XS_EINVAL;
+    if (!(theta[0] > 0.0) || !(theta[2 + m->n_species] > 0.0)) return XS_EINVAL;
+    cudaStream_t st = S(stream);
+    char* ws = (char*)workspace;
+    const int Sp = m->n_species;
+    const size_t LN = (size_t)m->L * (size_t)m->N;
+    const size_t es = (m->prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
+    double* F = F0 ? F0 : (double*)(ws + p.F0);
+    r = model_forward_impl(m, theta, F, ws, p, st);
+    if (r) return r;
+    double* T = (double*)(ws + p.T);
+    double* vmr = (double*)(ws + p.vmr);
+    char* sig = ws + p.sigma;
+    double* dtau = (double*)(ws + p.dtau);
+    double* gF = (double*)(ws + p.gF);
+    double* gdtau = (double*)(ws + p.gdtau);
+    double* gsig = (double*)(ws + p.gsig);
+    double* gvmr = (double*)(ws + p.gvmr);
+    double* gT = (double*)(ws + p.gT);
+    double* gTtmp = (double*)(ws + p.gTtmp);
+    double* gb = (double*)(ws + p.gb);
+    if ((r = xsi::rt_loglike(F, m->d_obs, m->sig_obs, m->N, out, gF, st))) return r;
+    if ((r = xsi::rt_emission_adjoint(gF, dtau, T, m->nu, m->L, m->N, gdtau, gT, ws + p.emws, st))) return r;
+    const void* sp[XS_MAX_SPECIES];
+    double* gsp[XS_MAX_SPECIES];
+    for (int s = 0; s < Sp; ++s) {
+        sp[s] = sig + es * LN * s;
+        gsp[s] = gsig + LN * s;
+    }
+    if ((r = xsi::rt_tau_adjoint(sp, Sp, vmr, m->P_bar, m->dP_bar, m->L, m->N, m->gravity, m->mu, m->prec, gdtau, gsp,
+                                 gvmr, st)))
+        return r;
+    for (int s = 0; s < Sp; ++s) {
+        r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec, nullptr,
+                        ws + p.xsws, p.xsws_bytes, true, gsp[s], gTtmp, gb + s, st);
+        if (r) return r;
+        if ((r = xsi::rt_accumulate(gT, gTtmp, m->L, 0, st))) return r;
+    }
+    return xsi::rt_theta_grad(Sp, m->L, theta[0], theta[1], theta + 2, theta[2 + Sp], T, m->P_bar, gT, gvmr, gb, out,
+                              st);
+}
+
+} // extern "C"

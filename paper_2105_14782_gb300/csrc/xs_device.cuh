@@ -1,0 +1,238 @@
+// Device-side building blocks of libxs: physical constants, the Faddeeva
+// function w(z) = exp(-z^2) erfc(-iz) by tiers (Sec. 2.1.1), and small helpers.
+//
+// Faddeeva tiers.  H = Re w is needed to a relative accuracy of ~1e-7 (FP32) or
+// ~1e-15 (FP64) everywhere, including the Gaussian-to-Lorentzian transition at
+// small a where Re w is far smaller than |w|.  Each tier keeps the real part free
+// of cancellation:
+//   * |z| large: the asymptotic series of Eq. asywofz,
+//       w ~ i/(sqrt(pi) z) * (1 + sum_{k>=1} (2k-1)!! (1/(2 z^2))^k),
+//     truncated at K terms chosen per |z| band (bands measured against an
+//     arbitrary-precision reference); with z = x + ia and 1/z = (x - ia)/|z|^2
+//     the real part is (a Re p - x Im p)/(sqrt(pi)|z|^2) with both terms of one
+//     sign, so it keeps its relative accuracy as a -> 0.
+//   * |z| small: the exponentially convergent series behind Eq. algo916 /
+//     algo916L (Zaghloul & Ali 2011).  Written with E_n^-+ = exp(-(nh -+ x)^2):
+//       Re w = e^{-x^2} [K(a) cos 2ax + (2h/pi) sin(ax) sin(ax)/a] + (a h/pi) Sc
+//       Im w = e^{-x^2} [-K(a) sin 2ax + (h/pi) sin(2ax)/a]       + (h/pi) Ss
+//       Sc = sum_n (E_n^- + E_n^+)/(n^2h^2 + a^2),  Ss = sum_n nh (E_n^- - E_n^+)/(n^2h^2 + a^2)
+//       K(a) = erfcx(a) - (2ah/pi) sum_n e^{-n^2h^2}/(n^2h^2 + a^2)   (per line, precomputed)
+//     Every E_n is taken directly from its own small exponent (no recurrence
+//     through e^{-x^2} e^{2nhx}, which would lose digits); only the n near x/h
+//     (and, for small x, the first E_n^+) are summed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace xsd {
+
+// CODATA 2018 (cgs) and the second radiation constant c2 as printed in Sec. 2.2.
+constexpr double kB = 1.380649e-16;
+constexpr double hP = 6.62607015e-27;
+constexpr double cL = 2.99792458e10;
+constexpr double amu = 1.66053906660e-24;
+constexpr double c2 = 1.4387773;
+constexpr double Tref = 296.0;
+constexpr double bar_per_atm = 1.01325;
+constexpr double PI = 3.14159265358979323846;
+constexpr double SQRTPI = 1.77245385090551602730;
+constexpr double INV_SQRTPI = 0.56418958354775628695;
+constexpr double SQRT2 = 1.41421356237309504880;
+
+// Scale applied to line strengths in the FP32 path so that partial sums of the
+// cross-section (1e-35 .. 1e-12 cm^2) sit well inside the normal float range.
+constexpr double MIXED_SCALE = 1208925819614629174706176.0; // 2^80
+constexpr double MIXED_UNSCALE = 8.27180612553027674871e-25; // 2^-80
+
+template <class R> struct vec4;
+template <> struct vec4<float> { using type = float4; };
+template <> struct vec4<double> { using type = double4_32a; };
+
+// Per-precision Faddeeva tier table.
+template <class R> struct Tier;
+template <> struct Tier<float> {
+    static constexpr float z2_far = 1.0e4f;    // |z| >= 100: K = 1 (closed real form)
+    static constexpr float z2_mid1 = 625.0f;   // |z| >= 25 : K = 2
+    static constexpr float z2_mid2 = 42.25f;   // |z| >= 6.5: K = 6, below: series
+    static constexpr int K1 = 1, K2 = 2, K3 = 6;
+    static constexpr float h = 0.7f;           // series step (error ~1e-8 relative)
+    static constexpr int nwin = 8;             // E_n^- kept for |n - x/h| <= nwin
+    static constexpr float tcut = 5.3f;        // E_n^+ kept while nh + x < tcut
+};
+template <> struct Tier<double> {
+    static constexpr double z2_far = 22500.0;  // |z| >= 150: K = 3
+    static constexpr double z2_mid1 = 1600.0;  // |z| >= 40 : K = 5
+    static constexpr double z2_mid2 = 100.0;   // |z| >= 10 : K = 12, below: series
+    static constexpr int K1 = 3, K2 = 5, K3 = 12;
+    static constexpr double h = 0.5;           // series step (error ~1e-17)
+    static constexpr int nwin = 13;
+    static constexpr double tcut = 6.5;
+};
+
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
+
+__device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+__device__ __forceinline__ int round_int(float v) { return __float2int_rn(v); }
+__device__ __forceinline__ int round_int(double v) { return __double2int_rn(v); }
+
+__device__ __forceinline__ float exp_neg(float t2) { return __expf(-t2); }
+__device__ __forceinline__ double exp_neg(double t2) { return exp(-t2); }
+
+__device__ __forceinline__ void sincos_r(float v, float* s, float* c) { sincosf(v, s, c); }
+__device__ __forceinline__ void sincos_r(double v, double* s, double* c) { sincos(v, s, c); }
+__device__ __forceinline__ float sin_r(float v) { return sinf(v); }
+__device__ __forceinline__ double sin_r(double v) { return sin(v); }
+
+// exp(-x^2) with x^2 split into hi + lo so the rounding of x*x does not enter.
+__device__ __forceinline__ float exp_negsq(float x)
+{
+    float hi = x * x;
+    float lo = fmaf(x, x, -hi);
+    return __expf(-hi) * (1.0f - lo);
+}
+__device__ __forceinline__ double exp_negsq(double x)
+{
+    double hi = x * x;
+    double lo = fma(x, x, -hi);
+    return exp(-hi) * (1.0 - lo);
+}
+
+// Asymptotic series (Eq. asywofz) with K correction terms; x >= 0, a >= 0,
+// r = 1/(x^2 + a^2).  Returns w.
+template <class R, int K>
+__device__ __forceinline__ void w_asym(R x, R a, R r, R* wr, R* wi)
+{
+    // u = 1/(2 z^2) = conj(z)^2 r^2 / 2
+    R hr2 = R(0.5) * r * r;
+    R ur = (x - a) * (x + a) * hr2;
+    R ui = R(-2) * a * x * hr2;
+    R pr = R(1), pi = R(0);
+#pragma unroll
+    for (int k = K; k >= 1; --k) {
+        R c = R(2 * k - 1);
+        R tr = ur * pr - ui * pi;
+        R ti = ur * pi + ui * pr;
+        pr = R(1) + c * tr;
+        pi = c * ti;
+    }
+    R s = r * R(INV_SQRTPI);
+    *wr = (a * pr - x * pi) * s;
+    *wi = (x * pr + a * pi) * s;
+}
+
+// Asymptotic series of w'(z) = dw/dz:  w' ~ -(2 i u / sqrt(pi)) (1 + sum_k (2k+1)!! u^k).
+template <class R, int K>
+__device__ __forceinline__ void dw_asym(R x, R a, R r, R* dr, R* di)
+{
+    R hr2 = R(0.5) * r * r;
+    R ur = (x - a) * (x + a) * hr2;
+    R ui = R(-2) * a * x * hr2;
+    R pr = R(1), pi = R(0);
+#pragma unroll
+    for (int k = K; k >= 1; --k) {
+        R c = R(2 * k + 1);
+        R tr = ur * pr - ui * pi;
+        R ti = ur * pi + ui * pr;
+        pr = R(1) + c * tr;
+        pi = c * ti;
+    }
+    // q = u p ; w' = -(2i/sqrt(pi)) q = (2/sqrt(pi)) (Im q - i Re q)
+    R qr = ur * pr - ui * pi;
+    R qi = ur * pi + ui * pr;
+    *dr = R(2 * INV_SQRTPI) * qi;
+    *di = R(-2 * INV_SQRTPI) * qr;
+}
+
+// Small-|z| series; x >= 0, a >= 0, Kc = K(a) for this precision's step h.
+template <class R>
+__device__ __forceinline__ void w_series(R x, R a, R Kc, R* wr, R* wi)
+{
+    const R h = Tier<R>::h;
+    const int nwin = Tier<R>::nwin;
+    R sc = R(0), ss = R(0);
+    int n0 = round_int(x / h);
+    R a2 = a * a;
+#pragma unroll 1
+    for (int k = -nwin; k <= nwin; ++k) {
+        int n = n0 + k;
+        if (n < 1) continue;
+        R nh = R(n) * h;
+        R t = nh - x;
+        R e = exp_neg(t * t);
+        R d = R(1) / fma(nh, nh, a2);
+        sc = fma(d, e, sc);
+        ss = fma(nh * d, e, ss);
+    }
+#pragma unroll 1
+    for (int n = 1; n <= 64; ++n) { // bounded even for non-finite x
+        R nh = R(n) * h;
+        R t = nh + x;
+        if (!(t < Tier<R>::tcut)) break;
+        R e = exp_neg(t * t);
+        R d = R(1) / fma(nh, nh, a2);
+        sc = fma(d, e, sc);
+        ss = fma(-nh * d, e, ss);
+    }
+    R ex = exp_negsq(x);
+    R s2, c2v;
+    sincos_r(R(2) * a * x, &s2, &c2v);
+    R sax = sin_r(a * x);
+    R sax_a = (a > R(0)) ? sax / a : x;
+    R s2_a = (a > R(0)) ? s2 / a : R(2) * x;
+    const R hpi = h * R(1.0 / PI);
+    *wr = ex * (Kc * c2v + R(2) * hpi * sax * sax_a) + a * hpi * sc;
+    *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
+}
+
+// w(x + ia) for any tier; x >= 0.
+template <class R>
+__device__ __forceinline__ void faddeeva(R x, R a, R Kc, R* wr, R* wi)
+{
+    R z2 = fma(x, x, a * a);
+    if (z2 >= Tier<R>::z2_mid2) {
+        R r = R(1) / z2;
+        if (z2 >= Tier<R>::z2_far)
+            w_asym<R, Tier<R>::K1>(x, a, r, wr, wi);
+        else if (z2 >= Tier<R>::z2_mid1)
+            w_asym<R, Tier<R>::K2>(x, a, r, wr, wi);
+        else
+            w_asym<R, Tier<R>::K3>(x, a, r, wr, wi);
+    } else {
+        w_series<R>(x, a, Kc, wr, wi);
+    }
+}
+
+// w and w' for any tier; x >= 0.
+template <class R>
+__device__ __forceinline__ void faddeeva_d(R x, R a, R Kc, R* wr, R* wi, R* dr, R* di)
+{
+    R z2 = fma(x, x, a * a);
+    if (z2 >= Tier<R>::z2_mid2) {
+        R r = R(1) / z2;
+        if (z2 >= Tier<R>::z2_far) {
+            w_asym<R, Tier<R>::K1>(x, a, r, wr, wi);
+            dw_asym<R, Tier<R>::K1>(x, a, r, dr, di);
+        } else if (z2 >= Tier<R>::z2_mid1) {
+            w_asym<R, Tier<R>::K2>(x, a, r, wr, wi);
+            dw_asym<R, Tier<R>::K2>(x, a, r, dr, di);
+        } else {
+            w_asym<R, Tier<R>::K3>(x, a, r, wr, wi);
+            dw_asym<R, Tier<R>::K3>(x, a, r, dr, di);
+        }
+    } else {
+        w_series<R>(x, a, Kc, wr, wi);
+        // w' = -2 z w + 2i/sqrt(pi)
+        *dr = R(-2) * (x * *wr - a * *wi);
+        *di = R(-2) * (x * *wi + a * *wr) + R(2 * INV_SQRTPI);
+    }
+}
+
+} // namespace xsd

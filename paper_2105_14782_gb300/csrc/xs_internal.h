@@ -1,0 +1,40 @@
+// Internal host-side interfaces shared by the translation units of libxs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/xs.h"
+
+namespace xsi {
+
+// line-sum forward (adjoint == false: writes sigma) or adjoint (writes g_T, g_b)
+int xs_run(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L, double sb,
+           double W, int prec, void* sigma, void* ws, size_t ws_bytes, bool adjoint, const double* g_sigma,
+           double* g_T, double* g_b, cudaStream_t st);
+
+// checks ascending (grid == false: non-decreasing centres; grid == true: strictly
+// increasing grid) on the device; blocks on `st`; flag_dev is one device int
+int check_sorted(const double* v, int64_t n, cudaStream_t st, int* flag_dev, bool grid);
+
+int rt_tau(const void* const* sigma, int32_t S, const double* vmr, const double* P, const double* dP, int32_t L,
+           int64_t N, double g, double mu, double kappa, int prec, double* dtau, cudaStream_t st);
+int rt_tau_adjoint(const void* const* sigma, int32_t S, const double* vmr, const double* P, const double* dP,
+                   int32_t L, int64_t N, double g, double mu, int prec, const double* g_dtau, double* const* g_sigma,
+                   double* g_vmr, cudaStream_t st);
+int rt_emission(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
+                cudaStream_t st);
+size_t rt_emission_ws(int32_t L, int64_t N);
+int rt_emission_adjoint(const double* g_F0, const double* dtau, const double* T, const double* nu, int32_t L,
+                        int64_t N, double* g_dtau, double* g_T, void* ws, cudaStream_t st);
+int rt_loglike(const double* F, const double* d, const double* s, int64_t N, double* logL, double* g_F,
+               cudaStream_t st);
+int rt_temperatures(double T0, double alpha, const double* P, int32_t L, double* T, cudaStream_t st);
+int rt_fill_vmr(const double* theta_dev_unused, int32_t S, int32_t L, const double* log10_vmr_host, double* vmr,
+                cudaStream_t st);
+int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* log10_vmr_host, double sb,
+                  const double* T, const double* P, const double* g_T, const double* g_vmr, const double* g_b,
+                  double* out, cudaStream_t st);
+int rt_accumulate(double* dst, const double* src, int64_t n, int first, cudaStream_t st);
+
+} // namespace xsi

@@ -1,0 +1,298 @@
+"""Thin ctypes binding of libxs (include/xs.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Device memory
+comes from PyTorch tensors; the stream is torch's current CUDA stream unless one
+is given.  There is no CPU fallback: without the compiled library or a GPU the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+XS_OK, XS_EINVAL, XS_EUNSORTED, XS_ENOMEM, XS_ECUDA, XS_ETIMEOUT = 0, -1, -2, -3, -4, -5
+PREC_FP64, PREC_MIXED = 0, 1
+MAX_SPECIES = 8
+
+_lib = None
+
+
+class XsError(RuntimeError):
+    def __init__(self, fn, code):
+        msg = lib().xs_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{fn} failed: {msg} ({code})")
+        self.code = code
+
+
+class XsLinesC(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nu_hat", C.c_void_p), ("ln_S0", C.c_void_p), ("elower", C.c_void_p),
+                ("gamma_ref", C.c_void_p), ("n_temp", C.c_void_p), ("mass_amu", C.c_double),
+                ("q_exponent", C.c_double)]
+
+
+class XsModelC(C.Structure):
+    _fields_ = [("n_species", C.c_int32), ("species", XsLinesC * MAX_SPECIES), ("nu", C.c_void_p),
+                ("N", C.c_int64), ("P_bar", C.c_void_p), ("dP_bar", C.c_void_p), ("L", C.c_int32),
+                ("wing_cut", C.c_double), ("gravity", C.c_double), ("mu", C.c_double), ("kappa_coef", C.c_double),
+                ("d_obs", C.c_void_p), ("sig_obs", C.c_void_p), ("prec", C.c_int)]
+
+
+def lib():
+    """Load libxs.so (building it first if the sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libxs.so is missing; run paper_2105_14782_gb300._build.build()")
+        L = C.CDLL(path)
+        vp, i64, i32, d, sz, i = C.c_void_p, C.c_int64, C.c_int32, C.c_double, C.c_size_t, C.c_int
+        L.xs_strerror.restype = C.c_char_p
+        L.xs_strerror.argtypes = [i]
+        L.xs_sort_lines_host.argtypes = [i64, vp, vp, vp, vp, vp]
+        L.xs_check_sorted.argtypes = [vp, i64, i, vp, vp]
+        L.xs_workspace_bytes.restype = sz
+        L.xs_workspace_bytes.argtypes = [i64, i64, i32, i]
+        L.xs_workspace_min_bytes.restype = sz
+        L.xs_workspace_min_bytes.argtypes = [i64, i64, i32, i]
+        L.xs_compute.argtypes = [C.POINTER(XsLinesC), vp, i64, vp, vp, i32, d, d, i, vp, vp, sz, vp]
+        L.xs_compute_adjoint.argtypes = [C.POINTER(XsLinesC), vp, i64, vp, vp, i32, d, d, i, vp, vp, vp, vp, sz, vp]
+        L.tau_layers.argtypes = [C.POINTER(vp), i32, vp, vp, vp, i32, i64, d, d, d, i, vp, vp]
+        L.tau_layers_adjoint.argtypes = [C.POINTER(vp), i32, vp, vp, vp, i32, i64, d, d, i, vp, C.POINTER(vp), vp, vp]
+        L.emission_spectrum.argtypes = [vp, vp, vp, i32, i64, vp, vp]
+        L.emission_workspace_bytes.restype = sz
+        L.emission_workspace_bytes.argtypes = [i32, i64]
+        L.emission_spectrum_adjoint.argtypes = [vp, vp, vp, vp, i32, i64, vp, vp, vp, sz, vp]
+        L.loglike_gauss.argtypes = [vp, vp, vp, i64, vp, vp, vp]
+        L.layer_temperatures.argtypes = [d, d, vp, i32, vp, vp]
+        L.xs_model_workspace_bytes.restype = sz
+        L.xs_model_workspace_bytes.argtypes = [C.POINTER(XsModelC)]
+        L.xs_model_forward.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
+        L.xs_model_logl_grad.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
+        _lib = L
+    return _lib
+
+
+def _check(fn, code):
+    if code != XS_OK:
+        raise XsError(fn, code)
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _dev(t):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.is_contiguous()):
+        raise ValueError("expected a contiguous CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _ws(nbytes, device):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+class DeviceLines:
+    """A line list sorted by centre (libxs's host sort) and resident on the GPU."""
+
+    def __init__(self, lines, device="cuda"):
+        arrs = [np.array(a, dtype=np.float64, copy=True) for a in lines.arrays()]
+        n = arrs[0].size
+        _check("xs_sort_lines_host", lib().xs_sort_lines_host(n, *[a.ctypes.data_as(C.c_void_p) for a in arrs]))
+        self.n = n
+        self.mass_amu = float(lines.mass_amu)
+        self.q_exponent = float(lines.q_exponent)
+        self.tensors = [torch.from_numpy(a).to(device) for a in arrs]
+        self.nu_hat, self.ln_S0, self.elower, self.gamma_ref, self.n_temp = self.tensors
+
+    def struct(self):
+        ptr = [t.data_ptr() if self.n else None for t in self.tensors]
+        return XsLinesC(self.n, *ptr, self.mass_amu, self.q_exponent)
+
+
+def check_sorted(v, strict=False, stream=None):
+    flag = torch.zeros(1, dtype=torch.int32, device=v.device)
+    return lib().xs_check_sorted(_dev(v), v.numel(), int(strict), _dev(flag), _stream(stream))
+
+
+def workspace_bytes(n_lines, N, L, prec):
+    return lib().xs_workspace_bytes(n_lines, N, L, prec)
+
+
+def xs_compute(lines: DeviceLines, nu, T, P_bar, broad_scale=1.0, wing_cut=25.0, prec=PREC_MIXED, out=None,
+               workspace=None, stream=None):
+    N, L = nu.numel(), T.numel()
+    dt = torch.float32 if prec == PREC_MIXED else torch.float64
+    if out is None:
+        out = torch.empty((L, N), dtype=dt, device=nu.device)
+    if workspace is None:
+        workspace = _ws(workspace_bytes(lines.n, N, L, prec), nu.device)
+    s = lines.struct()
+    _check("xs_compute", lib().xs_compute(C.byref(s), _dev(nu), N, _dev(T), _dev(P_bar), L, float(broad_scale),
+                                          float(wing_cut), prec, _dev(out), _dev(workspace), workspace.numel(),
+                                          _stream(stream)))
+    return out
+
+
+def xs_compute_adjoint(lines: DeviceLines, nu, T, P_bar, g_sigma, broad_scale=1.0, wing_cut=25.0, prec=PREC_MIXED,
+                       workspace=None, stream=None):
+    N, L = nu.numel(), T.numel()
+    g_T = torch.empty(L, dtype=torch.float64, device=nu.device)
+    g_b = torch.empty(1, dtype=torch.float64, device=nu.device)
+    if workspace is None:
+        workspace = _ws(workspace_bytes(lines.n, N, L, prec), nu.device)
+    s = lines.struct()
+    _check("xs_compute_adjoint", lib().xs_compute_adjoint(
+        C.byref(s), _dev(nu), N, _dev(T), _dev(P_bar), L, float(broad_scale), float(wing_cut), prec, _dev(g_sigma),
+        _dev(g_T), _dev(g_b), _dev(workspace), workspace.numel(), _stream(stream)))
+    return g_T, g_b
+
+
+def _ptrs(ts):
+    arr = (C.c_void_p * len(ts))(*[t.data_ptr() if t is not None else None for t in ts])
+    return arr
+
+
+def tau_layers(sigmas, vmr, P_bar, dP_bar, gravity=1e5, mu=2.313, kappa_coef=1e-8, prec=PREC_MIXED, stream=None):
+    L, N = sigmas[0].shape
+    dtau = torch.empty((L, N), dtype=torch.float64, device=P_bar.device)
+    _check("tau_layers", lib().tau_layers(_ptrs(sigmas), len(sigmas), _dev(vmr), _dev(P_bar), _dev(dP_bar), L, N,
+                                          float(gravity), float(mu), float(kappa_coef), prec, _dev(dtau),
+                                          _stream(stream)))
+    return dtau
+
+
+def tau_layers_adjoint(sigmas, vmr, P_bar, dP_bar, g_dtau, gravity=1e5, mu=2.313, prec=PREC_MIXED, stream=None):
+    L, N = sigmas[0].shape
+    gs = [torch.empty((L, N), dtype=torch.float64, device=P_bar.device) for _ in sigmas]
+    gv = torch.empty((len(sigmas), L), dtype=torch.float64, device=P_bar.device)
+    _check("tau_layers_adjoint", lib().tau_layers_adjoint(
+        _ptrs(sigmas), len(sigmas), _dev(vmr), _dev(P_bar), _dev(dP_bar), L, N, float(gravity), float(mu), prec,
+        _dev(g_dtau), _ptrs(gs), _dev(gv), _stream(stream)))
+    return gs, gv
+
+
+def emission_spectrum(dtau, T, nu, stream=None):
+    L, N = dtau.shape
+    F0 = torch.empty(N, dtype=torch.float64, device=dtau.device)
+    _check("emission_spectrum", lib().emission_spectrum(_dev(dtau), _dev(T), _dev(nu), L, N, _dev(F0),
+                                                        _stream(stream)))
+    return F0
+
+
+def emission_spectrum_adjoint(g_F0, dtau, T, nu, stream=None):
+    L, N = dtau.shape
+    g_dtau = torch.empty_like(dtau)
+    g_T = torch.empty(L, dtype=torch.float64, device=dtau.device)
+    ws = _ws(lib().emission_workspace_bytes(L, N), dtau.device)
+    _check("emission_spectrum_adjoint", lib().emission_spectrum_adjoint(
+        _dev(g_F0), _dev(dtau), _dev(T), _dev(nu), L, N, _dev(g_dtau), _dev(g_T), _dev(ws), ws.numel(),
+        _stream(stream)))
+    return g_dtau, g_T
+
+
+def loglike_gauss(F, d, s, stream=None):
+    out = torch.empty(1, dtype=torch.float64, device=F.device)
+    gF = torch.empty_like(F)
+    _check("loglike_gauss", lib().loglike_gauss(_dev(F), _dev(d), _dev(s), F.numel(), _dev(out), _dev(gF),
+                                                _stream(stream)))
+    return out, gF
+
+
+def layer_temperatures(T0, alpha, P_bar, stream=None):
+    T = torch.empty_like(P_bar)
+    _check("layer_temperatures", lib().layer_temperatures(float(T0), float(alpha), _dev(P_bar), P_bar.numel(),
+                                                          _dev(T), _stream(stream)))
+    return T
+
+
+class EmissionModel:
+    """Species line lists, grid, layers and (optionally) an observed spectrum,
+    resident on one GPU, with the composite forward and log-likelihood-gradient
+    calls of libxs.  theta = (T0, alpha, log10 vmr_0..log10 vmr_{S-1}, s_b)."""
+
+    def __init__(self, atm, prec=PREC_MIXED, device="cuda", d_obs=None, sig_obs=None, lines=None):
+        self.device = torch.device(device)
+        self.prec = prec
+        self.species = lines if lines is not None else [DeviceLines(sp, device) for sp in atm.species]
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.nu = torch.as_tensor(np.asarray(atm.nu), **f64)
+        self.P = torch.as_tensor(np.asarray(atm.p_bar), **f64)
+        self.dP = torch.as_tensor(np.asarray(atm.dp_bar), **f64)
+        self.atm = atm
+        self.S = len(self.species)
+        self.N, self.L = self.nu.numel(), self.P.numel()
+        self.d_obs = None if d_obs is None else torch.as_tensor(np.asarray(d_obs), **f64)
+        self.sig_obs = None if sig_obs is None else torch.as_tensor(np.asarray(sig_obs), **f64)
+        self._c = self._struct()
+        self.ws = _ws(lib().xs_model_workspace_bytes(C.byref(self._c)), self.device)
+        self.out = torch.empty(1 + 3 + self.S, **f64)
+        self.F0 = torch.empty(self.N, **f64)
+
+    def _struct(self):
+        sp = (XsLinesC * MAX_SPECIES)()
+        for i, s in enumerate(self.species):
+            sp[i] = s.struct()
+        a = self.atm
+        return XsModelC(self.S, sp, self.nu.data_ptr(), self.N, self.P.data_ptr(), self.dP.data_ptr(), self.L,
+                        float(a.wing_cut), float(a.gravity), float(a.mu), float(a.kappa_coef),
+                        None if self.d_obs is None else self.d_obs.data_ptr(),
+                        None if self.sig_obs is None else self.sig_obs.data_ptr(), self.prec)
+
+    def set_observation(self, d_obs, sig_obs):
+        f64 = dict(dtype=torch.float64, device=self.device)
+        self.d_obs = torch.as_tensor(d_obs, **f64).contiguous()
+        self.sig_obs = torch.as_tensor(sig_obs, **f64).contiguous()
+        self._c = self._struct()
+
+    def forward(self, theta, out=None, stream=None):
+        th = (C.c_double * len(theta))(*[float(v) for v in theta])
+        F0 = self.F0 if out is None else out
+        _check("xs_model_forward", lib().xs_model_forward(C.byref(self._c), th, _dev(F0), _dev(self.ws),
+                                                          self.ws.numel(), _stream(stream)))
+        return F0
+
+    def logl_grad_async(self, theta, out=None, F0=None, stream=None):
+        """Launches the forward + adjoint; returns the device tensor
+        [logL, dlogL/dtheta...] (valid once the stream reaches this point)."""
+        th = (C.c_double * len(theta))(*[float(v) for v in theta])
+        o = self.out if out is None else out
+        _check("xs_model_logl_grad", lib().xs_model_logl_grad(
+            C.byref(self._c), th, _dev(o), None if F0 is None else _dev(F0), _dev(self.ws), self.ws.numel(),
+            _stream(stream)))
+        return o
+
+    def logl_grad(self, theta, stream=None):
+        o = self.logl_grad_async(theta, stream=stream).cpu().numpy()
+        return float(o[0]), o[1:].copy()
+
+
+class SpectrumLogL(torch.autograd.Function):
+    """logL(theta) with the gradient from libxs's hand-written adjoint kernels."""
+
+    @staticmethod
+    def forward(ctx, theta, model):
+        th = theta.detach().cpu().double().tolist()
+        o = model.logl_grad_async(th).clone()
+        ctx.save_for_backward(o[1:].to(theta.device, theta.dtype))
+        return o[0:1].to(theta.device, theta.dtype).reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None
+
+
+def log_likelihood(theta, model):
+    return SpectrumLogL.apply(theta, model)
+
+
+LN10 = math.log(10.0)
