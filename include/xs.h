@@ -220,6 +220,18 @@ int xs_model_forward(const xs_model* model, const double* theta, double* F0, voi
 int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, double* F0, void* workspace,
                        size_t workspace_bytes, xs_stream stream);
 
+/*
+ * Diagnostics (no paper counterpart).  xs_profile(1) makes the library record a
+ * CUDA event pair around every line-sum kernel launch (forward and adjoint,
+ * on the launching stream) until xs_profile(0); xs_profile_read synchronises
+ * those events and returns the summed kernel times in ms and the launch counts
+ * since profiling was enabled.  xs_launch_count returns how many kernels the
+ * library has launched since it was loaded (host-side counter, all threads).
+ */
+int xs_profile(int enable);
+int xs_profile_read(double* fwd_ms, int64_t* fwd_launches, double* adj_ms, int64_t* adj_launches);
+uint64_t xs_launch_count(void);
+
 #ifdef __cplusplus
 }
 #endif

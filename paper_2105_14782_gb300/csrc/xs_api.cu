@@ -1,12 +1,100 @@
 // C ABI of libxs: argument checks, workspace plans and the composite model
 // calls.  Every entry point returns an xs_status and never throws or prints.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <numeric>
 #include <vector>
 
 #include "xs_internal.h"
+
+// ------------------------------------------------------------ diagnostics
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+std::mutex g_prof_mu;
+bool g_prof_on = false;
+struct ProfPair {
+    cudaEvent_t a, b;
+    int kind;
+};
+std::vector<ProfPair> g_prof;    // pairs recorded since profiling was enabled
+std::vector<cudaEvent_t> g_pool; // events kept for reuse
+cudaEvent_t take_event()
+{
+    if (!g_pool.empty()) {
+        cudaEvent_t e = g_pool.back();
+        g_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+int g_open_kind = -1;
+cudaEvent_t g_open_ev = nullptr;
+} // namespace
+
+namespace xsi {
+void count_launch(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+void prof_begin(int kind, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on) return;
+    g_open_ev = take_event();
+    g_open_kind = kind;
+    cudaEventRecord(g_open_ev, st);
+}
+void prof_end(int kind, cudaStream_t st)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_prof_on || g_open_ev == nullptr || g_open_kind != kind) return;
+    cudaEvent_t e = take_event();
+    cudaEventRecord(e, st);
+    g_prof.push_back({g_open_ev, e, kind});
+    g_open_ev = nullptr;
+    g_open_kind = -1;
+}
+} // namespace xsi
+
+extern "C" {
+
+int xs_profile(int enable)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    for (auto& p : g_prof) {
+        g_pool.push_back(p.a);
+        g_pool.push_back(p.b);
+    }
+    g_prof.clear();
+    g_prof_on = enable != 0;
+    return XS_OK;
+}
+
+int xs_profile_read(double* fwd_ms, int64_t* fwd_launches, double* adj_ms, int64_t* adj_launches)
+{
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    double t[2] = {0.0, 0.0};
+    int64_t c[2] = {0, 0};
+    for (auto& p : g_prof) {
+        if (cudaEventSynchronize(p.b) != cudaSuccess) return XS_ECUDA;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) return XS_ECUDA;
+        t[p.kind] += ms;
+        c[p.kind] += 1;
+    }
+    if (fwd_ms) *fwd_ms = t[0];
+    if (fwd_launches) *fwd_launches = c[0];
+    if (adj_ms) *adj_ms = t[1];
+    if (adj_launches) *adj_launches = c[1];
+    return XS_OK;
+}
+
+uint64_t xs_launch_count(void) { return g_launches.load(); }
+
+} // extern "C"
 
 namespace {
 

@@ -78,6 +78,23 @@ __device__ __forceinline__ float rcp_fast(float x)
 }
 __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 
+// x = |d| c with d = dh + dl and c = ch + cl as unevaluated float pairs:
+// returns x as a pair (xh, xl), xh = fl(|dh| ch).
+__device__ __forceinline__ void scaled_pair(float dh, float dl, float ch, float cl, float* xh, float* xl)
+{
+    float sgn = (dh < 0.0f) ? -1.0f : 1.0f;
+    dh *= sgn;
+    dl *= sgn;
+    float p = dh * ch;
+    *xh = p;
+    *xl = fmaf(dh, ch, -p) + fmaf(dh, cl, dl * ch);
+}
+__device__ __forceinline__ void scaled_pair(double dh, double, double ch, double, double* xh, double* xl)
+{
+    *xh = fabs(dh) * ch;
+    *xl = 0.0;
+}
+
 __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
 __device__ __forceinline__ int round_int(float v) { return __float2int_rn(v); }
@@ -151,10 +168,13 @@ __device__ __forceinline__ void dw_asym(R x, R a, R r, R* dr, R* di)
     *di = R(-2 * INV_SQRTPI) * qr;
 }
 
-// Small-|z| series; x >= 0, a >= 0, Kc = K(a) for this precision's step h.
+// Small-|z| series; x = xh + xl >= 0 (xl a small correction carrying the bits
+// of x a single float cannot: exp(-x^2) has condition number 2x^2 in x),
+// a >= 0, Kc = K(a) for this precision's step h.
 template <class R>
-__device__ __forceinline__ void w_series(R x, R a, R Kc, R* wr, R* wi)
+__device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
 {
+    const R x = xh;
     const R h = Tier<R>::h;
     const int nwin = Tier<R>::nwin;
     R sc = R(0), ss = R(0);
@@ -165,7 +185,7 @@ __device__ __forceinline__ void w_series(R x, R a, R Kc, R* wr, R* wi)
         int n = n0 + k;
         if (n < 1) continue;
         R nh = R(n) * h;
-        R t = nh - x;
+        R t = (nh - xh) - xl;
         R e = exp_neg(t * t);
         R d = R(1) / fma(nh, nh, a2);
         sc = fma(d, e, sc);
@@ -174,14 +194,14 @@ __device__ __forceinline__ void w_series(R x, R a, R Kc, R* wr, R* wi)
 #pragma unroll 1
     for (int n = 1; n <= 64; ++n) { // bounded even for non-finite x
         R nh = R(n) * h;
-        R t = nh + x;
+        R t = (nh + xh) + xl;
         if (!(t < Tier<R>::tcut)) break;
         R e = exp_neg(t * t);
         R d = R(1) / fma(nh, nh, a2);
         sc = fma(d, e, sc);
         ss = fma(-nh * d, e, ss);
     }
-    R ex = exp_negsq(x);
+    R ex = exp_negsq(xh) * (R(1) - R(2) * xh * xl);
     R s2, c2v;
     sincos_r(R(2) * a * x, &s2, &c2v);
     R sax = sin_r(a * x);
@@ -192,9 +212,9 @@ __device__ __forceinline__ void w_series(R x, R a, R Kc, R* wr, R* wi)
     *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
 }
 
-// w(x + ia) for any tier; x >= 0.
+// w(x + ia) for any tier; x = x + xl >= 0.
 template <class R>
-__device__ __forceinline__ void faddeeva(R x, R a, R Kc, R* wr, R* wi)
+__device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
@@ -206,13 +226,13 @@ __device__ __forceinline__ void faddeeva(R x, R a, R Kc, R* wr, R* wi)
         else
             w_asym<R, Tier<R>::K3>(x, a, r, wr, wi);
     } else {
-        w_series<R>(x, a, Kc, wr, wi);
+        w_series<R>(x, xl, a, Kc, wr, wi);
     }
 }
 
-// w and w' for any tier; x >= 0.
+// w and w' for any tier; x = x + xl >= 0.
 template <class R>
-__device__ __forceinline__ void faddeeva_d(R x, R a, R Kc, R* wr, R* wi, R* dr, R* di)
+__device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R* dr, R* di)
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
@@ -228,7 +248,7 @@ __device__ __forceinline__ void faddeeva_d(R x, R a, R Kc, R* wr, R* wi, R* dr, 
             dw_asym<R, Tier<R>::K3>(x, a, r, dr, di);
         }
     } else {
-        w_series<R>(x, a, Kc, wr, wi);
+        w_series<R>(x, xl, a, Kc, wr, wi);
         // w' = -2 z w + 2i/sqrt(pi)
         *dr = R(-2) * (x * *wr - a * *wi);
         *di = R(-2) * (x * *wi + a * *wr) + R(2 * INV_SQRTPI);

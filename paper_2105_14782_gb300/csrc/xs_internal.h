@@ -8,6 +8,12 @@
 
 namespace xsi {
 
+// host-side launch counter (every kernel launch site bumps it)
+void count_launch(int n = 1);
+// profiling event pairs around line-sum launches (kind 0 forward, 1 adjoint)
+void prof_begin(int kind, cudaStream_t st);
+void prof_end(int kind, cudaStream_t st);
+
 // line-sum forward (adjoint == false: writes sigma) or adjoint (writes g_T, g_b)
 int xs_run(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L, double sb,
            double W, int prec, void* sigma, void* ws, size_t ws_bytes, bool adjoint, const double* g_sigma,

@@ -89,8 +89,8 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
                                    const double* __restrict__ n_temp, int64_t nl, double mass, double qexp,
                                    const double* __restrict__ T, const double* __restrict__ P_bar, int layer0,
                                    double sb, double scale, typename vec4<R>::type* __restrict__ rec1,
-                                   typename vec4<R>::type* __restrict__ rec2, R* __restrict__ rec3,
-                                   float* __restrict__ agg)
+                                   typename vec4<R>::type* __restrict__ rec2, R* __restrict__ clo,
+                                   R* __restrict__ rec3, float* __restrict__ agg)
 {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = blockIdx.y;
@@ -132,6 +132,7 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
         v2.w = (R)Kc;
         rec1[idx] = v1;
         rec2[idx] = v2;
+        clo[idx] = (R)(c - (double)v2.x); // the part of c the rounded value misses
         if (rec3) {
             double u = c2 * nuh / Tn;
             double dlnS = c2 * elower[l] / (Tn * Tn) - qexp / Tn - (u / Tn) / expm1(u);
@@ -165,6 +166,12 @@ template <> struct Off<float> {
         *lo = (float)(o - (double)*hi);
     }
     __device__ static float dnu(float ohi, float olo, float bhi, float blo) { return (ohi - bhi) + (olo - blo); }
+    // (ohi - bhi) is exact when the point is near the line (Sterbenz); the lo parts ride along
+    __device__ static void dnu2(float ohi, float olo, float bhi, float blo, float* dh, float* dl)
+    {
+        *dh = ohi - bhi;
+        *dl = olo - blo;
+    }
 };
 template <> struct Off<double> {
     __device__ static void make(double v, double, double* hi, float* lo)
@@ -173,6 +180,11 @@ template <> struct Off<double> {
         *lo = 0.0f;
     }
     __device__ static double dnu(double ohi, float, double bhi, float) { return ohi - bhi; }
+    __device__ static void dnu2(double ohi, float, double bhi, float, double* dh, double* dl)
+    {
+        *dh = ohi - bhi;
+        *dl = 0.0;
+    }
 };
 
 __device__ __forceinline__ int64_t lb_jhi(const int2* jr, int64_t n, int v) // first l with jr[l].y >= v
@@ -200,6 +212,7 @@ struct LsShared {
     float blo[LS_TILE];
     typename vec4<R>::type r1[LS_TILE];
     typename vec4<R>::type r2[LS_TILE];
+    R clo[LS_TILE];
     int2 jr[LS_TILE];
     float olo[LS_WARPS][32 * LS_G];
     int64_t win[2];
@@ -209,7 +222,8 @@ template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
     const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
-    const float* __restrict__ agg, const double* __restrict__ nu, int64_t N, int64_t nl, int layer0, int ksplit,
+    const R* __restrict__ clo, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N, int64_t nl,
+    int layer0, int ksplit,
     double unscale, void* __restrict__ sigma, int sigma_is_float, double* __restrict__ partial, int L_total)
 {
     using R4 = typename vec4<R>::type;
@@ -284,6 +298,7 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
                 sh.blo[tid] = bl;
                 sh.r1[tid] = rec1[lay + l];
                 sh.r2[tid] = rec2[lay + l];
+                sh.clo[tid] = clo[lay + l];
                 sh.jr[tid] = jrange[l];
             } else {
                 // padding: a copy of the chunk's last line with zero amplitude, so
@@ -299,6 +314,7 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
                 z2.x = R(1); z2.y = R(1); z2.z = R(0); z2.w = R(0);
                 sh.r1[tid] = z1;
                 sh.r2[tid] = z2;
+                sh.clo[tid] = R(0);
                 sh.jr[tid] = jrange[ce - 1];
             }
         }
@@ -335,14 +351,16 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
                     const R bh = sh.bhi[li];
                     const float bl = sh.blo[li];
                     const R4 p2 = sh.r2[li];
+                    const R cl = sh.clo[li];
                     const int2 jr = sh.jr[li];
 #pragma unroll
                     for (int g = 0; g < LS_G; ++g) {
                         if (jg[g] >= jr.x && jg[g] <= jr.y) {
-                            R d = Off<R>::dnu(ohi[g], sh.olo[w][g * 32 + lane], bh, bl);
-                            R x = fabs(d) * p2.x;
+                            R dh, dl, x, xl;
+                            Off<R>::dnu2(ohi[g], sh.olo[w][g * 32 + lane], bh, bl, &dh, &dl);
+                            scaled_pair(dh, dl, p2.x, cl, &x, &xl);
                             R wr, wi;
-                            faddeeva<R>(x, p2.y, p2.w, &wr, &wi);
+                            faddeeva<R>(x, xl, p2.y, p2.w, &wr, &wi);
                             acc[g] = fma(p2.z, wr, acc[g]);
                         }
                     }
@@ -406,6 +424,7 @@ struct AdjShared {
     typename vec4<R>::type t[LS_TILE]; // fast form: f_T = rho (T1 + rho (T2 + rho (T3 + rho T4)))
     typename vec4<R>::type u[LS_TILE]; // fast form: f_b = rho (U1 + rho (U2 + rho (U3 + rho U4)))
     R G[LS_TILE];
+    R clo[LS_TILE];
     R aS[LS_TILE], nn[LS_TILE];
     int2 jr[LS_TILE];
     float olo[LS_WARPS][32 * LS_G];
@@ -421,7 +440,8 @@ template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
     const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
-    const R* __restrict__ rec3, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N,
+    const R* __restrict__ clo, const R* __restrict__ rec3, const float* __restrict__ agg, const double* __restrict__ nu,
+    int64_t N,
     int64_t nl, int layer0, int ksplit, const double* __restrict__ T, const double* __restrict__ g_sigma,
     double lam_scale, double* __restrict__ part, int nstrips)
 {
@@ -494,6 +514,7 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
                 R4 p1 = rec1[lay + l];
                 R aS = rec3[2 * (lay + l)], nn = rec3[2 * (lay + l) + 1];
                 sh.r2[tid] = rec2[lay + l];
+                sh.clo[tid] = clo[lay + l];
                 sh.jr[tid] = jrange[l];
                 sh.G[tid] = p1.x;
                 sh.aS[tid] = aS;
@@ -526,6 +547,7 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
                 sh.t[tid] = zz;
                 sh.u[tid] = zz;
                 sh.G[tid] = R(1);
+                sh.clo[tid] = R(0);
                 sh.aS[tid] = R(0);
                 sh.nn[tid] = R(0);
                 sh.jr[tid] = jrange[ce - 1];
@@ -569,14 +591,16 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
                     const R4 p2 = sh.r2[li];
                     const int2 jr = sh.jr[li];
                     const R aS = sh.aS[li], nn = sh.nn[li];
+                    const R cl = sh.clo[li];
 #pragma unroll
                     for (int g = 0; g < LS_G; ++g) {
                         if (jg[g] >= jr.x && jg[g] <= jr.y) {
-                            R d = Off<R>::dnu(ohi[g], sh.olo[w][g * 32 + lane], bh, bl);
-                            R x = fabs(d) * p2.x;
+                            R dh, dl, x, xl;
+                            Off<R>::dnu2(ohi[g], sh.olo[w][g * 32 + lane], bh, bl, &dh, &dl);
+                            scaled_pair(dh, dl, p2.x, cl, &x, &xl);
                             R a = p2.y;
                             R wr, wi, dr, di;
-                            faddeeva_d<R>(x, a, p2.w, &wr, &wi, &dr, &di);
+                            faddeeva_d<R>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
                             // H_x = Re w', H_a = -Im w'
                             R V0 = p2.z * wr;
                             R V1 = p2.z * x * dr;
@@ -676,7 +700,7 @@ int choose_ksplit(int64_t nl, int64_t N, int Lc)
 
 struct XsPlan {
     int prec, Lc, ksplit, nchunks;
-    size_t off_jr, off_agg, off_rec1, off_rec2, off_rec3, off_part, total;
+    size_t off_jr, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_part, total;
 };
 
 XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc, bool adjoint)
@@ -697,6 +721,8 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc, bool adjoint)
     off += align256(4 * rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
     p.off_rec3 = off;
     off += align256(2 * rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
+    p.off_clo = off;
+    off += align256(rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
     p.off_part = off;
     size_t fwd_part = (p.ksplit > 1) ? sizeof(double) * (size_t)p.ksplit * Lc * N : 0;
     size_t adj_part = sizeof(double) * 2 * (size_t)L * strips_of(N) * p.ksplit;
@@ -752,6 +778,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
     R4* rec1 = (R4*)(ws + p.off_rec1);
     R4* rec2 = (R4*)(ws + p.off_rec2);
     R* rec3 = (R*)(ws + p.off_rec3);
+    R* clo = (R*)(ws + p.off_clo);
     double* part = (double*)(ws + p.off_part);
     const int strips = strips_of(N);
 
@@ -767,32 +794,42 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
     }
     cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr);
     layer_agg_init_kernel<<<(2 * L + 255) / 256, 256, 0, st>>>(agg, 2 * L);
+    count_launch(2);
     for (int c = 0; c < p.nchunks; ++c) {
         int l0 = c * p.Lc;
         int lc = std::min(p.Lc, L - l0);
         dim3 pg((unsigned)((nl + 255) / 256), (unsigned)lc);
         line_params_kernel<R><<<pg, 256, 0, st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp, nl,
-                                                   ln->mass_amu, ln->q_exponent, T, P, l0, sb, scale, rec1, rec2,
+                                                   ln->mass_amu, ln->q_exponent, T, P, l0, sb, scale, rec1, rec2, clo,
                                                    adjoint ? rec3 : nullptr, agg);
+        count_launch();
         dim3 grid((unsigned)strips, (unsigned)lc, (unsigned)p.ksplit);
         R4* r1b = rec1;
         R4* r2b = rec2;
         R* r3b = rec3;
         if (!adjoint) {
+            prof_begin(0, st);
             linesum_kernel<R, std::is_same<R, float>::value><<<grid, LS_THREADS, 0, st>>>(
-                ln->nu_hat, jr, r1b, r2b, agg, nu, N, nl, l0, p.ksplit, unscale, sigma, mixed ? 1 : 0, part, lc);
+                ln->nu_hat, jr, r1b, r2b, clo, agg, nu, N, nl, l0, p.ksplit, unscale, sigma, mixed ? 1 : 0, part, lc);
+            prof_end(0, st);
+            count_launch();
             if (p.ksplit > 1) {
+                count_launch();
                 int64_t cnt = (int64_t)lc * N;
                 combine_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(part, p.ksplit, cnt, (int64_t)l0 * N,
                                                                               cnt, unscale, sigma, mixed ? 1 : 0);
             }
         } else {
+            prof_begin(1, st);
             linesum_adjoint_kernel<R, std::is_same<R, float>::value><<<grid, LS_THREADS, 0, st>>>(
-                ln->nu_hat, jr, r1b, r2b, r3b, agg, nu, N, nl, l0, p.ksplit, T, g_sigma, unscale, part, strips);
+                ln->nu_hat, jr, r1b, r2b, clo, r3b, agg, nu, N, nl, l0, p.ksplit, T, g_sigma, unscale, part, strips);
+            prof_end(1, st);
+            count_launch();
         }
     }
     if (adjoint) {
         adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit, 1.0, 1.0 / sb, g_T, g_b);
+        count_launch();
     }
     return (cudaGetLastError() == cudaSuccess) ? XS_OK : XS_ECUDA;
 }
@@ -816,6 +853,7 @@ int check_sorted(const double* nu_hat, int64_t n, cudaStream_t st, int* flag_dev
         grid_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nu_hat, n, flag_dev);
     else
         sorted_check_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nu_hat, n, flag_dev);
+    count_launch();
     int h = 0;
     if (cudaMemcpyAsync(&h, flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess) return XS_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return XS_ECUDA;

@@ -270,6 +270,11 @@ using namespace xsd;
 namespace xsi {
 
 static inline int last_status() { return cudaGetLastError() == cudaSuccess ? XS_OK : XS_ECUDA; }
+static inline int launched(int n)
+{
+    count_launch(n);
+    return last_status();
+}
 
 static unsigned grid_for(int64_t total)
 {
@@ -284,7 +289,7 @@ int rt_tau(const void* const* sigma, int32_t S, const double* vmr, const double*
     for (int m = 0; m < S; ++m) sp.p[m] = sigma[m];
     tau_kernel<<<grid_for((int64_t)L * N), RT_THREADS, 0, st>>>(sp, S, vmr, P, dP, L, N, g, mu, kappa,
                                                                  prec == XS_PREC_MIXED, dtau);
-    return last_status();
+    return launched(1);
 }
 
 int rt_tau_adjoint(const void* const* sigma, int32_t S, const double* vmr, const double* P, const double* dP,
@@ -299,14 +304,14 @@ int rt_tau_adjoint(const void* const* sigma, int32_t S, const double* vmr, const
         gp.p[m] = g_sigma ? g_sigma[m] : nullptr;
     }
     tau_adjoint_kernel<<<L, RT_THREADS, 0, st>>>(sp, gp, S, vmr, dP, L, N, g, mu, prec == XS_PREC_MIXED, g_dtau, g_vmr);
-    return last_status();
+    return launched(1);
 }
 
 int rt_emission(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
                 cudaStream_t st)
 {
     emission_kernel<<<(unsigned)((N + RT_THREADS - 1) / RT_THREADS), RT_THREADS, 0, st>>>(dtau, T, nu, L, N, F0);
-    return last_status();
+    return launched(1);
 }
 
 size_t rt_emission_ws(int32_t L, int64_t N)
@@ -322,20 +327,20 @@ int rt_emission_adjoint(const double* g_F0, const double* dtau, const double* T,
     double* part = (double*)ws;
     emission_adjoint_kernel<<<(unsigned)nb, RT_THREADS, 0, st>>>(g_F0, dtau, T, nu, L, N, g_dtau, part);
     layer_sum_kernel<<<L, RT_THREADS, 0, st>>>(part, (int)nb, L, g_T);
-    return last_status();
+    return launched(2);
 }
 
 int rt_loglike(const double* F, const double* d, const double* s, int64_t N, double* logL, double* g_F,
                cudaStream_t st)
 {
     loglike_kernel<<<1, 1024, 0, st>>>(F, d, s, N, logL, g_F);
-    return last_status();
+    return launched(1);
 }
 
 int rt_temperatures(double T0, double alpha, const double* P, int32_t L, double* T, cudaStream_t st)
 {
     temperature_kernel<<<(L + 127) / 128, 128, 0, st>>>(T0, alpha, P, L, T);
-    return last_status();
+    return launched(1);
 }
 
 int rt_fill_vmr(const double*, int32_t S, int32_t L, const double* lg, double* vmr, cudaStream_t st)
@@ -343,7 +348,7 @@ int rt_fill_vmr(const double*, int32_t S, int32_t L, const double* lg, double* v
     VmrArgs a{};
     for (int m = 0; m < S; ++m) a.lg[m] = lg[m];
     fill_vmr_kernel<<<(S * L + 127) / 128, 128, 0, st>>>(a, S, L, vmr);
-    return last_status();
+    return launched(1);
 }
 
 int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* lg, double sb, const double* T,
@@ -355,13 +360,13 @@ int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* l
     VmrArgs a{};
     for (int m = 0; m < S; ++m) a.lg[m] = lg[m];
     theta_grad_kernel<<<1, 32, 0, st>>>(S, L, T0, a, T, P, g_T, g_vmr, g_b, out);
-    return last_status();
+    return launched(1);
 }
 
 int rt_accumulate(double* dst, const double* src, int64_t n, int first, cudaStream_t st)
 {
     accumulate_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, src, n, first);
-    return last_status();
+    return launched(1);
 }
 
 } // namespace xsi

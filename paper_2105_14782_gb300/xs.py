@@ -76,6 +76,10 @@ def lib():
         L.xs_model_workspace_bytes.argtypes = [C.POINTER(XsModelC)]
         L.xs_model_forward.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
         L.xs_model_logl_grad.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
+        L.xs_profile.argtypes = [i]
+        L.xs_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int64)]
+        L.xs_launch_count.restype = C.c_uint64
         _lib = L
     return _lib
 
@@ -212,6 +216,22 @@ def layer_temperatures(T0, alpha, P_bar, stream=None):
     _check("layer_temperatures", lib().layer_temperatures(float(T0), float(alpha), _dev(P_bar), P_bar.numel(),
                                                           _dev(T), _stream(stream)))
     return T
+
+
+def profile(enable: bool):
+    """Start (True) or stop (False) event timing of the line-sum kernels."""
+    _check("xs_profile", lib().xs_profile(int(enable)))
+
+
+def profile_read():
+    """(forward ms, forward launches, adjoint ms, adjoint launches) since profile(True)."""
+    a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+    _check("xs_profile_read", lib().xs_profile_read(C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def launch_count() -> int:
+    return int(lib().xs_launch_count())
 
 
 class EmissionModel:

@@ -60,18 +60,28 @@ def test_emission_adjoint_matches_central_differences(xs):
     g_dtau, g_T = xs.emission_spectrum_adjoint(dev(lam), dev(dtau), dev(T), dev(nu))
     g_dtau, g_T = g_dtau.cpu().numpy(), g_T.cpu().numpy()
     f = lambda d, t: float(np.dot(lam, oracle.emission(d, t, nu)))
+
+    def richardson(fun, x0, h):
+        # central differences at h and h/2 combined to O(h^4), so a larger step
+        # keeps the rounding of f (~1e5 here) out of a small derivative
+        d1 = (fun(x0 + h) - fun(x0 - h)) / (2 * h)
+        d2 = (fun(x0 + h / 2) - fun(x0 - h / 2)) / h
+        return (4 * d2 - d1) / 3
+
     for (n, j) in [(0, 0), (5, 17), (11, 39)]:
-        h = 1e-5 * dtau[n, j]
-        dp, dm = dtau.copy(), dtau.copy()
-        dp[n, j] += h
-        dm[n, j] -= h
-        assert g_dtau[n, j] == pytest.approx((f(dp, T) - f(dm, T)) / (2 * h), rel=1e-6)
+        def fd_fun(v, n=n, j=j):
+            dd = dtau.copy()
+            dd[n, j] = v
+            return f(dd, T)
+        fd = richardson(fd_fun, dtau[n, j], 1e-2 * dtau[n, j])
+        assert g_dtau[n, j] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(g_dtau).max())
     for n in [0, 6, 11]:
-        h = 1e-4 * T[n]
-        tp, tm = T.copy(), T.copy()
-        tp[n] += h
-        tm[n] -= h
-        assert g_T[n] == pytest.approx((f(dtau, tp) - f(dtau, tm)) / (2 * h), rel=1e-6)
+        def ft_fun(v, n=n):
+            tt = T.copy()
+            tt[n] = v
+            return f(dtau, tt)
+        fd = richardson(ft_fun, T[n], 1e-2 * T[n])
+        assert g_T[n] == pytest.approx(fd, rel=1e-6, abs=1e-9 * np.abs(g_T).max())
 
 
 def test_loglike_and_temperatures(xs):
