@@ -52,6 +52,8 @@ template <> struct vec4<double> { using type = double4_32a; };
 // Per-precision Faddeeva tier table.
 template <class R> struct Tier;
 template <> struct Tier<float> {
+    static constexpr float z2_fast = 625.0f;   // |z| >= 25: line-sum fast form (K = 2, real, per-line coefficients)
+    static constexpr float z2_fast_adj = 1600.0f; // |z| >= 40: adjoint fast form (K = 1; error < 2e-6 of a term)
     static constexpr float z2_far = 1.0e4f;    // |z| >= 100: K = 1 (closed real form)
     static constexpr float z2_mid1 = 625.0f;   // |z| >= 25 : K = 2
     static constexpr float z2_mid2 = 42.25f;   // |z| >= 6.5: K = 6, below: series
@@ -61,6 +63,8 @@ template <> struct Tier<float> {
     static constexpr float tcut = 5.3f;        // E_n^+ kept while nh + x < tcut
 };
 template <> struct Tier<double> {
+    static constexpr double z2_fast = 1e300;   // no truncated fast form in double precision
+    static constexpr double z2_fast_adj = 1e300;
     static constexpr double z2_far = 22500.0;  // |z| >= 150: K = 3
     static constexpr double z2_mid1 = 1600.0;  // |z| >= 40 : K = 5
     static constexpr double z2_mid2 = 100.0;   // |z| >= 10 : K = 12, below: series
@@ -82,12 +86,16 @@ __device__ __forceinline__ double rcp_fast(double x) { return 1.0 / x; }
 // returns x as a pair (xh, xl), xh = fl(|dh| ch).
 __device__ __forceinline__ void scaled_pair(float dh, float dl, float ch, float cl, float* xh, float* xl)
 {
-    float sgn = (dh < 0.0f) ? -1.0f : 1.0f;
-    dh *= sgn;
-    dl *= sgn;
-    float p = dh * ch;
+    // renormalise d = dh + dl first (Fast2Sum, |dl| << |dh| or both tiny) so that
+    // xh, which the asymptotic tiers use alone, carries all of d's leading bits
+    float d = dh + dl;
+    float e = (dh - d) + dl;
+    float sgn = (d < 0.0f) ? -1.0f : 1.0f;
+    d *= sgn;
+    e *= sgn;
+    float p = d * ch;
     *xh = p;
-    *xl = fmaf(dh, ch, -p) + fmaf(dh, cl, dl * ch);
+    *xl = fmaf(d, ch, -p) + fmaf(d, cl, e * ch);
 }
 __device__ __forceinline__ void scaled_pair(double dh, double, double ch, double, double* xh, double* xl)
 {
@@ -100,7 +108,8 @@ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? 
 __device__ __forceinline__ int round_int(float v) { return __float2int_rn(v); }
 __device__ __forceinline__ int round_int(double v) { return __double2int_rn(v); }
 
-__device__ __forceinline__ float exp_neg(float t2) { return __expf(-t2); }
+// accurate expf (a few ulp): the small-|z| tier is rare, and its exponent can reach ~40
+__device__ __forceinline__ float exp_neg(float t2) { return expf(-t2); }
 __device__ __forceinline__ double exp_neg(double t2) { return exp(-t2); }
 
 __device__ __forceinline__ void sincos_r(float v, float* s, float* c) { sincosf(v, s, c); }
@@ -113,7 +122,7 @@ __device__ __forceinline__ float exp_negsq(float x)
 {
     float hi = x * x;
     float lo = fmaf(x, x, -hi);
-    return __expf(-hi) * (1.0f - lo);
+    return expf(-hi) * (1.0f - lo);
 }
 __device__ __forceinline__ double exp_negsq(double x)
 {
@@ -187,7 +196,7 @@ __device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
         R nh = R(n) * h;
         R t = (nh - xh) - xl;
         R e = exp_neg(t * t);
-        R d = R(1) / fma(nh, nh, a2);
+        R d = rcp_fast(fma(nh, nh, a2));
         sc = fma(d, e, sc);
         ss = fma(nh * d, e, ss);
     }
@@ -197,7 +206,7 @@ __device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
         R t = (nh + xh) + xl;
         if (!(t < Tier<R>::tcut)) break;
         R e = exp_neg(t * t);
-        R d = R(1) / fma(nh, nh, a2);
+        R d = rcp_fast(fma(nh, nh, a2));
         sc = fma(d, e, sc);
         ss = fma(-nh * d, e, ss);
     }
@@ -218,7 +227,7 @@ __device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
-        R r = R(1) / z2;
+        R r = rcp_fast(z2);
         if (z2 >= Tier<R>::z2_far)
             w_asym<R, Tier<R>::K1>(x, a, r, wr, wi);
         else if (z2 >= Tier<R>::z2_mid1)
@@ -236,7 +245,7 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
-        R r = R(1) / z2;
+        R r = rcp_fast(z2);
         if (z2 >= Tier<R>::z2_far) {
             w_asym<R, Tier<R>::K1>(x, a, r, wr, wi);
             dw_asym<R, Tier<R>::K1>(x, a, r, dr, di);
@@ -253,6 +262,21 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
         *dr = R(-2) * (x * *wr - a * *wi);
         *di = R(-2) * (x * *wi + a * *wr) + R(2 * INV_SQRTPI);
     }
+}
+
+// Out-of-line entry points for the per-point tiered evaluation, so the hot
+// loops that call them stay small in the instruction cache.
+template <class R>
+__device__ __noinline__ R voigt_H(R x, R xl, R a, R Kc)
+{
+    R wr, wi;
+    faddeeva<R>(x, xl, a, Kc, &wr, &wi);
+    return wr;
+}
+template <class R>
+__device__ __noinline__ void voigt_w_dw(R x, R xl, R a, R Kc, R* w4)
+{
+    faddeeva_d<R>(x, xl, a, Kc, &w4[0], &w4[1], &w4[2], &w4[3]);
 }
 
 } // namespace xsd

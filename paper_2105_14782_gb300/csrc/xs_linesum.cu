@@ -30,7 +30,9 @@ constexpr int LS_THREADS = 128;
 constexpr int LS_WARPS = 4;
 constexpr int LS_G = 8;
 constexpr int LS_STRIP = LS_WARPS * 32 * LS_G; // 1024
-constexpr int LS_TILE = LS_THREADS;            // lines per shared-memory tile
+// resident CTAs per SM the register budget targets (FP32: 96 registers; FP64 keeps more)
+template <class R> struct MinBlocks { static constexpr int v = 5; };
+template <> struct MinBlocks<double> { static constexpr int v = 3; };
 
 // ------------------------------------------------------------------ K0: cut ranges
 
@@ -98,12 +100,12 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
     if (l < nl) {
         double Tn = T[layer0 + n], Pn = P_bar[layer0 + n];
         double nuh = nu_hat[l];
-        double qr = pow(Tn / Tref, qexp);
-        double boltz = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref));
-        double stim = expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref);
-        double S = boltz / qr * stim;
+        double lnTr = log(Tn / Tref);
+        // S(T) of Eq. Slog with Q(T)/Q(Tref) = (T/Tref)^q folded into one exponent
+        double S = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref) - qexp * lnTr) *
+                   (expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref));
         double beta = sqrt(kB * Tn / (mass * amu)) * nuh / cL;
-        double gam = sb * gamma_ref[l] * pow(Tn / Tref, -n_temp[l]) * (Pn / bar_per_atm);
+        double gam = sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (Pn / bar_per_atm);
         double s = S * scale;
         double B = 2.0 * beta * beta, G = gam * gam;
         double c = 1.0 / (SQRT2 * beta);
@@ -114,7 +116,8 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
         if (a * a < (double)Tier<R>::z2_mid2) {
             const double h = (double)Tier<R>::h;
             double s1 = 0.0;
-            for (int k = 1; k <= 40; ++k) {
+            const int kmax = (int)(6.3 / h) + 1; // e^{-(kh)^2} < 1e-17 beyond
+            for (int k = 1; k <= kmax; ++k) {
                 double kh = k * h;
                 s1 += exp(-kh * kh) / (kh * kh + a * a);
             }
@@ -155,8 +158,8 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
 
 // ------------------------------------------------------------------ K2: line sum
 
-// Offsets: FP32 path keeps nu relative to the strip reference as hi + lo floats;
-// FP64 path keeps absolute doubles.
+// Offsets: the FP32 path keeps nu relative to a reference point (the warp's
+// middle grid point) as hi + lo floats; the FP64 path keeps absolute doubles.
 template <class R> struct Off;
 template <> struct Off<float> {
     __device__ static void make(double v, double ref, float* hi, float* lo)
@@ -165,7 +168,6 @@ template <> struct Off<float> {
         *hi = (float)o;
         *lo = (float)(o - (double)*hi);
     }
-    __device__ static float dnu(float ohi, float olo, float bhi, float blo) { return (ohi - bhi) + (olo - blo); }
     // (ohi - bhi) is exact when the point is near the line (Sterbenz); the lo parts ride along
     __device__ static void dnu2(float ohi, float olo, float bhi, float blo, float* dh, float* dl)
     {
@@ -179,7 +181,6 @@ template <> struct Off<double> {
         *hi = v;
         *lo = 0.0f;
     }
-    __device__ static double dnu(double ohi, float, double bhi, float) { return ohi - bhi; }
     __device__ static void dnu2(double ohi, float, double bhi, float, double* dh, double* dl)
     {
         *dh = ohi - bhi;
@@ -206,74 +207,156 @@ __device__ __forceinline__ int64_t lb_jlo(const int2* jr, int64_t n, int v) // f
     return lo;
 }
 
-template <class R>
-struct LsShared {
-    R bhi[LS_TILE];
-    float blo[LS_TILE];
-    typename vec4<R>::type r1[LS_TILE];
-    typename vec4<R>::type r2[LS_TILE];
-    R clo[LS_TILE];
-    int2 jr[LS_TILE];
-    float olo[LS_WARPS][32 * LS_G];
-    int64_t win[2];
-};
-
-template <class R, bool FAST>
-__global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
-    const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
-    const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
-    const R* __restrict__ clo, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N, int64_t nl,
-    int layer0, int ksplit,
-    double unscale, void* __restrict__ sigma, int sigma_is_float, double* __restrict__ partial, int L_total)
+// Line window of a strip (all lines with an in-cut point in [j0, jlast]) and
+// the kc-th of ksplit equal parts of it, rounded to whole 32-line chunks.
+// Lane 0 searches, the warp gets the result by shuffle.
+__device__ __forceinline__ void strip_window(const int2* jrange, int64_t nl, int64_t j0, int64_t jlast, int ksplit,
+                                             int kc, int64_t* cb, int64_t* ce)
 {
-    using R4 = typename vec4<R>::type;
-    __shared__ LsShared<R> sh;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
-    const int64_t j0 = (int64_t)strip * LS_STRIP;
-    const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
-    const double ref = nu[min64(jlast, j0 + LS_STRIP / 2)];
-
-    if (tid == 0) {
-        int64_t b = lb_jhi(jrange, nl, (int)j0);
-        int64_t e = lb_jlo(jrange, nl, (int)jlast);
-        if (e < b) e = b;
-        int64_t len = e - b;
-        int64_t per = (len + ksplit - 1) / ksplit;
+    long long b = 0, e = 0;
+    if ((threadIdx.x & 31) == 0) {
+        int64_t bb = lb_jhi(jrange, nl, (int)j0);
+        int64_t ee = lb_jlo(jrange, nl, (int)jlast);
+        if (ee < bb) ee = bb;
+        int64_t per = (ee - bb + ksplit - 1) / ksplit;
         per = (per + 31) & ~(int64_t)31;
-        int64_t cb = min64(e, b + per * kc), ce = min64(e, cb + per);
-        sh.win[0] = cb;
-        sh.win[1] = ce;
+        b = min64(ee, bb + per * kc);
+        e = min64(ee, b + per);
     }
+    *cb = __shfl_sync(0xffffffffu, b, 0);
+    *ce = __shfl_sync(0xffffffffu, e, 0);
+}
 
+// Grid points of one warp: G per lane, lane-interleaved, offsets to the warp's
+// middle point.  Returns false when the warp has no point in the grid.
+template <class R>
+struct WarpPoints {
     R ohi[LS_G];
     int jg[LS_G];
-#pragma unroll
-    for (int g = 0; g < LS_G; ++g) {
-        int64_t j = j0 + w * (32 * LS_G) + g * 32 + lane;
-        int64_t jc = min64(j, jlast);
-        jg[g] = (int)j;
-        float lo;
-        Off<R>::make(nu[jc], ref, &ohi[g], &lo);
-        sh.olo[w][g * 32 + lane] = lo;
-    }
-    // the warp's point span (first and last valid point) for tile classification
-    const int jw0 = (int)min64(jlast, j0 + w * (32 * LS_G));
-    const int jw1 = (int)min64(jlast, j0 + w * (32 * LS_G) + 32 * LS_G - 1);
-    R ow0 = __shfl_sync(0xffffffffu, ohi[0], 0);
-    R ow1 = ohi[LS_G - 1];
+    int jw0, jw1; // first and last valid point of the warp
+    R ow0, ow1;   // their offsets
+    double ref;
+
+    __device__ bool init(const double* nu, int64_t jbase, int64_t jlast, float* olo_s)
     {
-        // last valid point of the warp may be in a lower (g, lane) slot
-        int jl = jw1 - (int)(j0 + w * (32 * LS_G));
-        int gl = jl >> 5, ll = jl & 31;
+        const int lane = threadIdx.x & 31;
+        if (jbase > jlast) return false;
+        ref = nu[min64(jlast, jbase + 16 * LS_G)];
+#pragma unroll
+        for (int g = 0; g < LS_G; ++g) {
+            int64_t j = jbase + g * 32 + lane;
+            jg[g] = (int)j;
+            float lo;
+            Off<R>::make(nu[min64(j, jlast)], ref, &ohi[g], &lo);
+            olo_s[g * 32 + lane] = lo;
+        }
+        jw0 = (int)jbase;
+        jw1 = (int)min64(jlast, jbase + 32 * LS_G - 1);
+        ow0 = __shfl_sync(0xffffffffu, ohi[0], 0);
+        int jl = jw1 - (int)jbase, gl = jl >> 5, ll = jl & 31;
         R v = ohi[0];
 #pragma unroll
         for (int g = 0; g < LS_G; ++g)
             if (g == gl) v = ohi[g];
         ow1 = __shfl_sync(0xffffffffu, v, ll);
+        return true;
     }
-    const float cmin = agg[2 * (layer0 + nloc)];
-    const float amin = agg[2 * (layer0 + nloc) + 1];
+};
+
+// Lower bound of |z| over the warp's points for lines [bf, bl] (offsets, sorted):
+// true when every point is at |z|^2 >= z2 from every line.
+__device__ __forceinline__ bool all_far(float bf, float bl, float ow0, float ow1, float cmin, float amin, float z2)
+{
+    float dist = fmaxf(fmaxf(bf - ow1, ow0 - bl), 0.0f);
+    float xm = dist * cmin;
+    return fmaf(xm, xm, amin * amin) >= z2;
+}
+
+template <class R>
+struct LineTile {
+    R bhi[32];
+    float blo[32];
+    R G[32], k0[32];
+    typename vec4<R>::type k[32]; // k1..k4 of the fast form
+    typename vec4<R>::type r2[32];
+    R clo[32];
+    int2 jr[32];
+};
+
+// Fast form of a line's term from the asymptotic series with K = 2 (Eq. asywofz),
+// written in rho = 1/(dnu^2 + gamma^2):  Av H = rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
+// with k0 = s gamma/pi = Al, B = 2 beta^2, G = gamma^2 and
+//   k1 = 1.5 B Al,  k2 = Al (3.75 B^2 - 2 G B),  k3 = -15 G B^2 Al,  k4 = 12 G^2 B^2 Al.
+// From rec1 = {G, Al, F1 = 1.5 B Al, F2 = -2 G B Al} and c = 1/sqrt(B):
+template <class R>
+__device__ __forceinline__ void fast_coeffs(const typename vec4<R>::type& p1, R c, R* k0,
+                                            typename vec4<R>::type* k)
+{
+    R B = rcp_fast(c * c);
+    *k0 = p1.y;
+    k->x = p1.z;
+    k->y = fma(R(2.5) * B, p1.z, p1.w);
+    k->z = R(7.5) * B * p1.w;
+    k->w = R(-6) * p1.x * B * p1.w;
+}
+
+// one lane's line record as loaded from global memory
+template <class R>
+struct LineRec {
+    double nu;
+    typename vec4<R>::type p1, p2;
+    R cl;
+    int2 jr;
+
+    __device__ void load(const double* nu_hat, const int2* jrange, const typename vec4<R>::type* rec1,
+                         const typename vec4<R>::type* rec2, const R* clo, int64_t l, int64_t ce)
+    {
+        if (l < ce) {
+            nu = nu_hat[l];
+            p1 = rec1[l];
+            p2 = rec2[l];
+            cl = clo[l];
+            jr = jrange[l];
+        } else {
+            // padding: the chunk's last line with zero amplitude keeps every
+            // sub-tile test and offset that of real lines
+            nu = nu_hat[ce - 1];
+            jr = jrange[ce - 1];
+            p1.x = R(1); p1.y = R(0); p1.z = R(0); p1.w = R(0);
+            p2.x = R(1); p2.y = R(1); p2.z = R(0); p2.w = R(0);
+            cl = R(0);
+        }
+    }
+};
+
+template <class R, bool FAST>
+__global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
+    const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
+    const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
+    const R* __restrict__ clo, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N, int64_t nl,
+    int layer0, int ksplit, double unscale, void* __restrict__ sigma, int sigma_is_float, double* __restrict__ partial,
+    int L_total)
+{
+    using R4 = typename vec4<R>::type;
+    __shared__ LineTile<R> tiles[LS_WARPS];
+    __shared__ float olo_s[LS_WARPS][32 * LS_G];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
+    const int64_t j0 = (int64_t)strip * LS_STRIP;
+    const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
+    LineTile<R>& tl = tiles[w];
+    float* olo = olo_s[w];
+
+    WarpPoints<R> pts;
+    if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast, olo)) return;
+    int64_t cb, ce;
+    strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
+    const int layer = layer0 + nloc;
+    const float cmin = agg[2 * layer], amin = agg[2 * layer + 1];
+    const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
+    const R4* r1g = rec1 + lay;
+    const R4* r2g = rec2 + lay;
+    const R* clg = clo + lay;
 
     R acc[LS_G], shi[LS_G], slo[LS_G];
 #pragma unroll
@@ -282,116 +365,118 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_kernel(
         shi[g] = R(0);
         slo[g] = R(0);
     }
-    __syncthreads();
-    const int64_t cb = sh.win[0], ce = sh.win[1];
-    const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
+    LineRec<R> nx;
+    if (cb < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, cb + lane, ce);
 
-    for (int64_t t0 = cb; t0 < ce; t0 += LS_TILE) {
+    for (int64_t t0 = cb; t0 < ce; t0 += 32) {
         {
-            int64_t l = t0 + tid;
-            if (l < ce) {
-                double v = nu_hat[l];
-                R bh;
-                float bl;
-                Off<R>::make(v, ref, &bh, &bl);
-                sh.bhi[tid] = bh;
-                sh.blo[tid] = bl;
-                sh.r1[tid] = rec1[lay + l];
-                sh.r2[tid] = rec2[lay + l];
-                sh.clo[tid] = clo[lay + l];
-                sh.jr[tid] = jrange[l];
-            } else {
-                // padding: a copy of the chunk's last line with zero amplitude, so
-                // the sub-tile tests and the offsets stay those of real lines
-                double v = nu_hat[ce - 1];
-                R bh;
-                float bl;
-                Off<R>::make(v, ref, &bh, &bl);
-                sh.bhi[tid] = bh;
-                sh.blo[tid] = bl;
-                R4 z1, z2;
-                z1.x = R(1); z1.y = R(0); z1.z = R(0); z1.w = R(0);
-                z2.x = R(1); z2.y = R(1); z2.z = R(0); z2.w = R(0);
-                sh.r1[tid] = z1;
-                sh.r2[tid] = z2;
-                sh.clo[tid] = R(0);
-                sh.jr[tid] = jrange[ce - 1];
-            }
+            R bh;
+            float bl;
+            Off<R>::make(nx.nu, pts.ref, &bh, &bl);
+            tl.bhi[lane] = bh;
+            tl.blo[lane] = bl;
+            R k0;
+            R4 kk;
+            fast_coeffs<R>(nx.p1, nx.p2.x, &k0, &kk);
+            tl.G[lane] = nx.p1.x;
+            tl.k0[lane] = k0;
+            tl.k[lane] = kk;
+            tl.r2[lane] = nx.p2;
+            tl.clo[lane] = nx.cl;
+            tl.jr[lane] = nx.jr;
         }
-        __syncthreads();
-        const int nt = (int)min64(LS_TILE, ce - t0);
-        for (int s0 = 0; s0 < nt; s0 += 32) {
-            bool fast = false;
-            if (FAST) {
-                const int sl = s0 + 31;
-                bool incut = (sh.jr[sl].x <= jw0) && (sh.jr[s0].y >= jw1);
-                float bf = (float)sh.bhi[s0], bl = (float)sh.bhi[sl];
-                float dist = fmaxf(fmaxf(bf - (float)ow1, (float)ow0 - bl), 0.0f);
-                float xm = dist * cmin;
-                fast = incut && (fmaf(xm, xm, amin * amin) >= (float)Tier<R>::z2_far);
-            }
-            if (fast) {
-#pragma unroll 4
-                for (int i = 0; i < 32; ++i) {
-                    const R b = sh.bhi[s0 + i];
-                    const R4 p = sh.r1[s0 + i];
+        __syncwarp();
+        if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, t0 + 32 + lane, ce); // in flight meanwhile
+
+        bool fast = false;
+        if (FAST) {
+            bool incut = (tl.jr[31].x <= pts.jw0) && (tl.jr[0].y >= pts.jw1);
+            fast = incut && all_far((float)tl.bhi[0], (float)tl.bhi[31], (float)pts.ow0, (float)pts.ow1, cmin, amin,
+                                    (float)Tier<R>::z2_fast);
+        }
+        if (fast) {
+#pragma unroll 2
+            for (int i = 0; i < 32; ++i) {
+                const R b = tl.bhi[i], G = tl.G[i], k0 = tl.k0[i];
+                const R4 k = tl.k[i];
 #pragma unroll
-                    for (int g = 0; g < LS_G; ++g) {
-                        R d = ohi[g] - b;
-                        R rho = rcp_fast(fma(d, d, p.x));
-                        R u = fma(p.w, rho, p.z);
-                        R q = fma(rho, u, p.y);
-                        acc[g] = fma(rho, q, acc[g]);
-                    }
+                for (int g = 0; g < LS_G; ++g) {
+                    R d = pts.ohi[g] - b;
+                    R rho = rcp_fast(fma(d, d, G));
+                    R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
+                    acc[g] = fma(rho, u, acc[g]);
                 }
-            } else {
-                const int ns = min(32, nt - s0);
-                for (int i = 0; i < ns; ++i) {
-                    const int li = s0 + i;
-                    const R bh = sh.bhi[li];
-                    const float bl = sh.blo[li];
-                    const R4 p2 = sh.r2[li];
-                    const R cl = sh.clo[li];
-                    const int2 jr = sh.jr[li];
+            }
+        } else {
+            // Per line (warp-uniform): if every point of the warp is at |z| >= 100
+            // use the Lorentz-wing form, masked by the cut only when the line does
+            // not cover the whole warp; else choose the Faddeeva tier per point.
+            for (int i = 0; i < 32; ++i) {
+                const R bh = tl.bhi[i];
+                const R4 p2 = tl.r2[i];
+                const int2 jr = tl.jr[i];
+                const R G = tl.G[i], k0 = tl.k0[i];
+                const R4 k = tl.k[i];
+                bool line_far = false;
+                if (FAST)
+                    line_far = all_far((float)bh, (float)bh, (float)pts.ow0, (float)pts.ow1, (float)p2.x, (float)p2.y,
+                                       (float)Tier<R>::z2_fast);
+                if (line_far) {
+                    const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
 #pragma unroll
                     for (int g = 0; g < LS_G; ++g) {
-                        if (jg[g] >= jr.x && jg[g] <= jr.y) {
+                        R d = pts.ohi[g] - bh;
+                        R rho = rcp_fast(fma(d, d, G));
+                        R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
+                        R v = rho * u;
+                        if (full || (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y)) acc[g] += v;
+                    }
+                } else {
+                    const float bl = tl.blo[i];
+                    const R cl = tl.clo[i];
+#pragma unroll
+                    for (int g = 0; g < LS_G; ++g) {
+                        if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
                             R dh, dl, x, xl;
-                            Off<R>::dnu2(ohi[g], sh.olo[w][g * 32 + lane], bh, bl, &dh, &dl);
+                            Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
                             scaled_pair(dh, dl, p2.x, cl, &x, &xl);
-                            R wr, wi;
-                            faddeeva<R>(x, xl, p2.y, p2.w, &wr, &wi);
-                            acc[g] = fma(p2.z, wr, acc[g]);
+                            if (FAST && fma(x, x, p2.y * p2.y) >= (R)Tier<R>::z2_fast) {
+                                R d = dh + dl;
+                                R rho = rcp_fast(fma(d, d, G));
+                                R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
+                                acc[g] = fma(rho, u, acc[g]);
+                            } else {
+                                acc[g] = fma(p2.z, voigt_H<R>(x, xl, p2.y, p2.w), acc[g]);
+                            }
                         }
                     }
                 }
             }
-            // fold the 32-line partial into the running compensated sum
-#pragma unroll
-            for (int g = 0; g < LS_G; ++g) {
-                R sres = shi[g] + acc[g];
-                R bb = sres - shi[g];
-                slo[g] += (shi[g] - (sres - bb)) + (acc[g] - bb);
-                shi[g] = sres;
-                acc[g] = R(0);
-            }
         }
-        __syncthreads();
+        // fold the 32-line partial into the running compensated sum (TwoSum)
+#pragma unroll
+        for (int g = 0; g < LS_G; ++g) {
+            R sres = shi[g] + acc[g];
+            R bb = sres - shi[g];
+            slo[g] += (shi[g] - (sres - bb)) + (acc[g] - bb);
+            shi[g] = sres;
+            acc[g] = R(0);
+        }
+        __syncwarp();
     }
 
-    const int layer = layer0 + nloc;
 #pragma unroll
     for (int g = 0; g < LS_G; ++g) {
-        if (jg[g] <= jlast) {
+        if (pts.jg[g] <= jlast) {
             double v = (double)shi[g] + (double)slo[g];
-            size_t o = (size_t)layer * N + jg[g];
+            size_t o = (size_t)layer * N + pts.jg[g];
             if (ksplit == 1) {
                 if (sigma_is_float)
                     ((float*)sigma)[o] = (float)(v * unscale);
                 else
                     ((double*)sigma)[o] = v * unscale;
             } else {
-                partial[((size_t)kc * L_total + nloc) * N + jg[g]] = v; // [ksplit][chunk layers][N]
+                partial[((size_t)kc * L_total + nloc) * N + pts.jg[g]] = v; // [ksplit][chunk layers][N]
             }
         }
     }
@@ -417,110 +502,82 @@ __global__ void combine_kernel(const double* __restrict__ partial, int ksplit, i
 // ------------------------------------------------------------------ K6: adjoint
 
 template <class R>
-struct AdjShared {
-    R bhi[LS_TILE];
-    float blo[LS_TILE];
-    typename vec4<R>::type r2[LS_TILE];
-    typename vec4<R>::type t[LS_TILE]; // fast form: f_T = rho (T1 + rho (T2 + rho (T3 + rho T4)))
-    typename vec4<R>::type u[LS_TILE]; // fast form: f_b = rho (U1 + rho (U2 + rho (U3 + rho U4)))
-    R G[LS_TILE];
-    R clo[LS_TILE];
-    R aS[LS_TILE], nn[LS_TILE];
-    int2 jr[LS_TILE];
-    float olo[LS_WARPS][32 * LS_G];
-    double red[2][LS_WARPS];
-    int64_t win[2];
+struct AdjTile {
+    R bhi[32];
+    float blo[32];
+    typename vec4<R>::type r2[32];
+    typename vec4<R>::type t[32]; // fast form: f_T = rho (T1 + rho (T2 + rho (T3 + rho T4)))
+    typename vec4<R>::type u[32]; // fast form: f_b = rho (U1 + rho (U2 + rho (U3 + rho U4)))
+    R G[32], clo[32], aS[32], nn[32];
+    int2 jr[32];
 };
 
 // Per evaluation the adjoint accumulates
 //   f_T = (dlnS/dT) V0 + (1/(2T)) D_beta + (-n/T) D_gamma   and   f_b = D_gamma
 // with V0 = Av H, D_beta = beta d sigma/d beta = -Av (H + x H_x + a H_a),
 // D_gamma = gamma d sigma/d gamma = Av a H_a, weighted by lambda_j = g_sigma[n][j].
+// In the Lorentz-wing form (K = 1 of the asymptotic series, rho = 1/(dnu^2 + gamma^2),
+// B = 2 beta^2, G = gamma^2, Al = s gamma/pi):
+//   V0 = Al (rho + 1.5 B rho^2 - 2 G B rho^3),  D_beta = Al B (3 rho^2 - 4 G rho^3),
+//   D_gamma = Al (rho + (1.5 B - 2 G) rho^2 - 12 G B rho^3 + 12 G^2 B rho^4).
 template <class R, bool FAST>
-__global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
+__global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_kernel(
     const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
     const R* __restrict__ clo, const R* __restrict__ rec3, const float* __restrict__ agg, const double* __restrict__ nu,
-    int64_t N,
-    int64_t nl, int layer0, int ksplit, const double* __restrict__ T, const double* __restrict__ g_sigma,
+    int64_t N, int64_t nl, int layer0, int ksplit, const double* __restrict__ T, const double* __restrict__ g_sigma,
     double lam_scale, double* __restrict__ part, int nstrips)
 {
     using R4 = typename vec4<R>::type;
-    __shared__ AdjShared<R> sh;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+    __shared__ AdjTile<R> tiles[LS_WARPS];
+    __shared__ float olo_s[LS_WARPS][32 * LS_G];
+    __shared__ double red[2][LS_WARPS];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
     const int layer = layer0 + nloc;
     const int64_t j0 = (int64_t)strip * LS_STRIP;
     const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
-    const double ref = nu[min64(jlast, j0 + LS_STRIP / 2)];
-    const double Tn = T[layer];
-    const R half_invT = (R)(0.5 / Tn);
+    const R half_invT = (R)(0.5 / T[layer]);
+    AdjTile<R>& tl = tiles[w];
+    float* olo = olo_s[w];
 
-    if (tid == 0) {
-        int64_t b = lb_jhi(jrange, nl, (int)j0);
-        int64_t e = lb_jlo(jrange, nl, (int)jlast);
-        if (e < b) e = b;
-        int64_t len = e - b;
-        int64_t per = (len + ksplit - 1) / ksplit;
-        per = (per + 31) & ~(int64_t)31;
-        int64_t cb = min64(e, b + per * kc), ce = min64(e, cb + per);
-        sh.win[0] = cb;
-        sh.win[1] = ce;
-    }
-    R ohi[LS_G], lam[LS_G];
-    int jg[LS_G];
-#pragma unroll
-    for (int g = 0; g < LS_G; ++g) {
-        int64_t j = j0 + w * (32 * LS_G) + g * 32 + lane;
-        int64_t jc = min64(j, jlast);
-        jg[g] = (int)j;
-        float lo;
-        Off<R>::make(nu[jc], ref, &ohi[g], &lo);
-        sh.olo[w][g * 32 + lane] = lo;
-        lam[g] = (j <= jlast) ? (R)(g_sigma[(size_t)layer * N + j] * lam_scale) : R(0);
-    }
-    const int jw0 = (int)min64(jlast, j0 + w * (32 * LS_G));
-    const int jw1 = (int)min64(jlast, j0 + w * (32 * LS_G) + 32 * LS_G - 1);
-    R ow0 = __shfl_sync(0xffffffffu, ohi[0], 0);
-    R ow1;
-    {
-        int jl = jw1 - (int)(j0 + w * (32 * LS_G));
-        int gl = jl >> 5, ll = jl & 31;
-        R v = ohi[0];
+    double sT = 0.0, sB = 0.0;
+    WarpPoints<R> pts;
+    if (pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast, olo)) {
+        int64_t cb, ce;
+        strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
+        const float cmin = agg[2 * layer], amin = agg[2 * layer + 1];
+        const size_t lay = (size_t)nloc * nl;
+        const R4* r1g = rec1 + lay;
+        const R4* r2g = rec2 + lay;
+        const R* clg = clo + lay;
+        const R* r3g = rec3 + 2 * lay;
+        R lam[LS_G];
 #pragma unroll
         for (int g = 0; g < LS_G; ++g)
-            if (g == gl) v = ohi[g];
-        ow1 = __shfl_sync(0xffffffffu, v, ll);
-    }
-    const float cmin = agg[2 * layer];
-    const float amin = agg[2 * layer + 1];
+            lam[g] = (pts.jg[g] <= jlast) ? (R)(g_sigma[(size_t)layer * N + pts.jg[g]] * lam_scale) : R(0);
 
-    R accT = R(0), accB = R(0);
-    double sT = 0.0, sB = 0.0;
-    __syncthreads();
-    const int64_t cb = sh.win[0], ce = sh.win[1];
-    const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
-
-    for (int64_t t0 = cb; t0 < ce; t0 += LS_TILE) {
-        {
-            int64_t l = t0 + tid;
-            if (l < ce) {
-                double v = nu_hat[l];
+        LineRec<R> nx;
+        R naS = R(0), nnn = R(0);
+        if (cb < ce) {
+            nx.load(nu_hat, jrange, r1g, r2g, clg, cb + lane, ce);
+            if (cb + lane < ce) {
+                naS = r3g[2 * (cb + lane)];
+                nnn = r3g[2 * (cb + lane) + 1];
+            }
+        }
+        R accT = R(0), accB = R(0);
+        for (int64_t t0 = cb; t0 < ce; t0 += 32) {
+            {
                 R bh;
                 float bl;
-                Off<R>::make(v, ref, &bh, &bl);
-                sh.bhi[tid] = bh;
-                sh.blo[tid] = bl;
-                R4 p1 = rec1[lay + l];
-                R aS = rec3[2 * (lay + l)], nn = rec3[2 * (lay + l) + 1];
-                sh.r2[tid] = rec2[lay + l];
-                sh.clo[tid] = clo[lay + l];
-                sh.jr[tid] = jrange[l];
-                sh.G[tid] = p1.x;
-                sh.aS[tid] = aS;
-                sh.nn[tid] = nn;
-                // fast-form coefficients from G, Al, F1 = 1.5 B Al, F2 = -2 G B Al
-                R G = p1.x, Al = p1.y, F1 = p1.z, F2 = p1.w;
+                Off<R>::make(nx.nu, pts.ref, &bh, &bl);
+                tl.bhi[lane] = bh;
+                tl.blo[lane] = bl;
+                tl.r2[lane] = nx.p2;
+                tl.clo[lane] = nx.cl;
+                tl.jr[lane] = nx.jr;
+                const R G = nx.p1.x, Al = nx.p1.y, F1 = nx.p1.z, F2 = nx.p1.w, aS = naS, nn = nnn;
                 R4 tc, uc;
                 tc.x = Al * (aS + nn);
                 tc.y = aS * F1 + half_invT * R(2) * F1 + nn * (F1 - R(2) * G * Al);
@@ -530,51 +587,35 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
                 uc.y = F1 - R(2) * G * Al;
                 uc.z = R(6) * F2;
                 uc.w = R(-6) * G * F2;
-                sh.t[tid] = tc;
-                sh.u[tid] = uc;
-            } else {
-                double v = nu_hat[ce - 1];
-                R bh;
-                float bl;
-                Off<R>::make(v, ref, &bh, &bl);
-                sh.bhi[tid] = bh;
-                sh.blo[tid] = bl;
-                R4 z2;
-                z2.x = R(1); z2.y = R(1); z2.z = R(0); z2.w = R(0);
-                sh.r2[tid] = z2;
-                R4 zz;
-                zz.x = R(0); zz.y = R(0); zz.z = R(0); zz.w = R(0);
-                sh.t[tid] = zz;
-                sh.u[tid] = zz;
-                sh.G[tid] = R(1);
-                sh.clo[tid] = R(0);
-                sh.aS[tid] = R(0);
-                sh.nn[tid] = R(0);
-                sh.jr[tid] = jrange[ce - 1];
+                tl.t[lane] = tc;
+                tl.u[lane] = uc;
+                tl.G[lane] = G;
+                tl.aS[lane] = aS;
+                tl.nn[lane] = nn;
             }
-        }
-        __syncthreads();
-        const int nt = (int)min64(LS_TILE, ce - t0);
-        for (int s0 = 0; s0 < nt; s0 += 32) {
+            __syncwarp();
+            if (t0 + 32 < ce) {
+                int64_t l = t0 + 32 + lane;
+                nx.load(nu_hat, jrange, r1g, r2g, clg, l, ce);
+                naS = (l < ce) ? r3g[2 * l] : R(0);
+                nnn = (l < ce) ? r3g[2 * l + 1] : R(0);
+            }
             bool fast = false;
             if (FAST) {
-                const int sl = s0 + 31;
-                bool incut = (sh.jr[sl].x <= jw0) && (sh.jr[s0].y >= jw1);
-                float bf = (float)sh.bhi[s0], bl = (float)sh.bhi[sl];
-                float dist = fmaxf(fmaxf(bf - (float)ow1, (float)ow0 - bl), 0.0f);
-                float xm = dist * cmin;
-                fast = incut && (fmaf(xm, xm, amin * amin) >= (float)Tier<R>::z2_far);
+                bool incut = (tl.jr[31].x <= pts.jw0) && (tl.jr[0].y >= pts.jw1);
+                fast = incut && all_far((float)tl.bhi[0], (float)tl.bhi[31], (float)pts.ow0, (float)pts.ow1, cmin,
+                                        amin, (float)Tier<R>::z2_fast_adj);
             }
             if (fast) {
 #pragma unroll 2
                 for (int i = 0; i < 32; ++i) {
-                    const R b = sh.bhi[s0 + i];
-                    const R G = sh.G[s0 + i];
-                    const R4 tc = sh.t[s0 + i];
-                    const R4 uc = sh.u[s0 + i];
+                    const R b = tl.bhi[i];
+                    const R G = tl.G[i];
+                    const R4 tc = tl.t[i];
+                    const R4 uc = tl.u[i];
 #pragma unroll
                     for (int g = 0; g < LS_G; ++g) {
-                        R d = ohi[g] - b;
+                        R d = pts.ohi[g] - b;
                         R rho = rcp_fast(fma(d, d, G));
                         R ft = rho * fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x);
                         R fb = rho * fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x);
@@ -583,32 +624,52 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
                     }
                 }
             } else {
-                const int ns = min(32, nt - s0);
-                for (int i = 0; i < ns; ++i) {
-                    const int li = s0 + i;
-                    const R bh = sh.bhi[li];
-                    const float bl = sh.blo[li];
-                    const R4 p2 = sh.r2[li];
-                    const int2 jr = sh.jr[li];
-                    const R aS = sh.aS[li], nn = sh.nn[li];
-                    const R cl = sh.clo[li];
+                for (int i = 0; i < 32; ++i) {
+                    const R bh = tl.bhi[i];
+                    const R4 p2 = tl.r2[i];
+                    const int2 jr = tl.jr[i];
+                    bool line_far = false;
+                    if (FAST)
+                        line_far = all_far((float)bh, (float)bh, (float)pts.ow0, (float)pts.ow1, (float)p2.x,
+                                           (float)p2.y, (float)Tier<R>::z2_fast_adj);
+                    if (line_far) {
+                        const R G = tl.G[i];
+                        const R4 tc = tl.t[i];
+                        const R4 uc = tl.u[i];
+                        const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
 #pragma unroll
-                    for (int g = 0; g < LS_G; ++g) {
-                        if (jg[g] >= jr.x && jg[g] <= jr.y) {
-                            R dh, dl, x, xl;
-                            Off<R>::dnu2(ohi[g], sh.olo[w][g * 32 + lane], bh, bl, &dh, &dl);
-                            scaled_pair(dh, dl, p2.x, cl, &x, &xl);
-                            R a = p2.y;
-                            R wr, wi, dr, di;
-                            faddeeva_d<R>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
-                            // H_x = Re w', H_a = -Im w'
-                            R V0 = p2.z * wr;
-                            R V1 = p2.z * x * dr;
-                            R V2 = -p2.z * a * di;
-                            R Db = -(V0 + V1 + V2);
-                            R ft = aS * V0 + half_invT * Db + nn * V2;
-                            accT = fma(lam[g], ft, accT);
-                            accB = fma(lam[g], V2, accB);
+                        for (int g = 0; g < LS_G; ++g) {
+                            R d = pts.ohi[g] - bh;
+                            R rho = rcp_fast(fma(d, d, G));
+                            R ft = rho * fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x);
+                            R fb = rho * fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x);
+                            R lm = (full || (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y)) ? lam[g] : R(0);
+                            accT = fma(lm, ft, accT);
+                            accB = fma(lm, fb, accB);
+                        }
+                    } else {
+                        const float bl = tl.blo[i];
+                        const R cl = tl.clo[i];
+                        const R aS = tl.aS[i], nn = tl.nn[i];
+#pragma unroll
+                        for (int g = 0; g < LS_G; ++g) {
+                            if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
+                                R dh, dl, x, xl;
+                                Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
+                                scaled_pair(dh, dl, p2.x, cl, &x, &xl);
+                                R a = p2.y;
+                                R w4[4];
+                                voigt_w_dw<R>(x, xl, a, p2.w, w4);
+                                const R wr = w4[0], dr = w4[2], di = w4[3];
+                                // H_x = Re w', H_a = -Im w'
+                                R V0 = p2.z * wr;
+                                R V1 = p2.z * x * dr;
+                                R V2 = -p2.z * a * di;
+                                R Db = -(V0 + V1 + V2);
+                                R ft = aS * V0 + half_invT * Db + nn * V2;
+                                accT = fma(lam[g], ft, accT);
+                                accB = fma(lam[g], V2, accB);
+                            }
                         }
                     }
                 }
@@ -617,8 +678,8 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
             sB += (double)accB;
             accT = R(0);
             accB = R(0);
+            __syncwarp();
         }
-        __syncthreads();
     }
     // fixed-order block reduction
     for (int o = 16; o > 0; o >>= 1) {
@@ -626,15 +687,15 @@ __global__ void __launch_bounds__(LS_THREADS) linesum_adjoint_kernel(
         sB += __shfl_xor_sync(0xffffffffu, sB, o);
     }
     if (lane == 0) {
-        sh.red[0][w] = sT;
-        sh.red[1][w] = sB;
+        red[0][w] = sT;
+        red[1][w] = sB;
     }
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         double a = 0.0, b = 0.0;
         for (int i = 0; i < LS_WARPS; ++i) {
-            a += sh.red[0][i];
-            b += sh.red[1][i];
+            a += red[0][i];
+            b += red[1][i];
         }
         size_t o = ((size_t)layer * nstrips + strip) * ksplit + kc;
         part[2 * o] = a;
