@@ -221,6 +221,81 @@ __device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
     *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
 }
 
+// FP32 small-|z| series with the E_n^- taken by a two-way recurrence from the
+// term nearest the peak, n0 = round(x/h), where t = n0 h - x = delta is small:
+//   E_{n0+k} = E_{n0+k-1} e^{-2h delta} q^{2k-1},  E_{n0-k} = E_{n0-k+1} e^{+2h delta} q^{2k-1},
+//   q = e^{-h^2};
+// every factor has a small exponent, so no digits are lost to e^{-x^2} e^{2nhx}.
+// Terms with |k| > 6 are below 1e-9 of the peak term.
+__device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float Kc, float* wr, float* wi)
+{
+    const float h = Tier<float>::h;
+    const int nw = 6;
+    // q^(2k-1), q = exp(-h^2) with h = 0.7f
+    const float Q[6] = {0.61262643f, 0.22992550f, 0.08629359f, 0.03238694f, 0.012155180f, 0.0045619742f};
+    const float x = xh;
+    const float a2 = a * a;
+    const int n0 = __float2int_rn(x / h);
+    const float delta = fmaf((float)n0, h, -xh) - xl;
+    const float E0 = expf(-delta * delta);
+    const float P = expf(-2.0f * h * delta);
+    const float Pi = 1.0f / P;
+    float sc = 0.0f, ss = 0.0f;
+    if (n0 >= 1) {
+        float nh = (float)n0 * h;
+        float d = rcp_fast(fmaf(nh, nh, a2));
+        sc = d * E0;
+        ss = nh * d * E0;
+    }
+    float Eu = E0, Ed = E0;
+#pragma unroll
+    for (int k = 1; k <= nw; ++k) {
+        Eu = Eu * P * Q[k - 1];
+        Ed = Ed * Pi * Q[k - 1];
+        float nhu = (float)(n0 + k) * h;
+        float du = rcp_fast(fmaf(nhu, nhu, a2));
+        sc = fmaf(du, Eu, sc);
+        ss = fmaf(nhu * du, Eu, ss);
+        int nd = n0 - k;
+        if (nd >= 1) {
+            float nhd = (float)nd * h;
+            float dd = rcp_fast(fmaf(nhd, nhd, a2));
+            sc = fmaf(dd, Ed, sc);
+            ss = fmaf(nhd * dd, Ed, ss);
+        }
+    }
+#pragma unroll 1
+    for (int n = 1; n <= 16; ++n) {
+        float nh = (float)n * h;
+        float t = (nh + xh) + xl;
+        if (!(t < Tier<float>::tcut)) break;
+        float e = expf(-t * t);
+        float d = rcp_fast(fmaf(nh, nh, a2));
+        sc = fmaf(d, e, sc);
+        ss = fmaf(-nh * d, e, ss);
+    }
+    float ex = exp_negsq(xh) * (1.0f - 2.0f * xh * xl);
+    float s2, c2v;
+    sincosf(2.0f * a * x, &s2, &c2v);
+    float sax = sinf(a * x);
+    float sax_a = (a > 0.0f) ? sax / a : x;
+    float s2_a = (a > 0.0f) ? s2 / a : 2.0f * x;
+    const float hpi = h * (float)(1.0 / PI);
+    *wr = ex * (Kc * c2v + 2.0f * hpi * sax * sax_a) + a * hpi * sc;
+    *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
+}
+
+template <class R>
+__device__ __forceinline__ void w_small(R x, R xl, R a, R Kc, R* wr, R* wi)
+{
+    w_series<R>(x, xl, a, Kc, wr, wi);
+}
+template <>
+__device__ __forceinline__ void w_small<float>(float x, float xl, float a, float Kc, float* wr, float* wi)
+{
+    w_series_rec(x, xl, a, Kc, wr, wi);
+}
+
 // w(x + ia) for any tier; x = x + xl >= 0.
 template <class R>
 __device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
@@ -235,7 +310,7 @@ __device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
         else
             w_asym<R, Tier<R>::K3>(x, a, r, wr, wi);
     } else {
-        w_series<R>(x, xl, a, Kc, wr, wi);
+        w_small<R>(x, xl, a, Kc, wr, wi);
     }
 }
 
@@ -257,7 +332,7 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
             dw_asym<R, Tier<R>::K3>(x, a, r, dr, di);
         }
     } else {
-        w_series<R>(x, xl, a, Kc, wr, wi);
+        w_small<R>(x, xl, a, Kc, wr, wi);
         // w' = -2 z w + 2i/sqrt(pi)
         *dr = R(-2) * (x * *wr - a * *wi);
         *di = R(-2) * (x * *wi + a * *wr) + R(2 * INV_SQRTPI);

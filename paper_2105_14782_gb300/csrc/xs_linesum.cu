@@ -276,7 +276,7 @@ template <class R>
 struct LineTile {
     R bhi[32];
     float blo[32];
-    R G[32], k0[32];
+    R G[32], k0[32], f2[32];
     typename vec4<R>::type k[32]; // k1..k4 of the fast form
     typename vec4<R>::type r2[32];
     R clo[32];
@@ -380,6 +380,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
             fast_coeffs<R>(nx.p1, nx.p2.x, &k0, &kk);
             tl.G[lane] = nx.p1.x;
             tl.k0[lane] = k0;
+            tl.f2[lane] = nx.p1.w;
             tl.k[lane] = kk;
             tl.r2[lane] = nx.p2;
             tl.clo[lane] = nx.cl;
@@ -388,13 +389,33 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
         __syncwarp();
         if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, t0 + 32 + lane, ce); // in flight meanwhile
 
-        bool fast = false;
+        // chunk class: 2 = every (line, point) at |z| >= 100 (K = 1 form),
+        // 1 = at |z| >= 25 (K = 2 form), 0 = mixed (per line, per point)
+        int cls = 0;
         if (FAST) {
             bool incut = (tl.jr[31].x <= pts.jw0) && (tl.jr[0].y >= pts.jw1);
-            fast = incut && all_far((float)tl.bhi[0], (float)tl.bhi[31], (float)pts.ow0, (float)pts.ow1, cmin, amin,
-                                    (float)Tier<R>::z2_fast);
+            if (incut) {
+                float dist = fmaxf(fmaxf((float)tl.bhi[0] - (float)pts.ow1, (float)pts.ow0 - (float)tl.bhi[31]), 0.0f);
+                float xm = dist * cmin;
+                float z2 = fmaf(xm, xm, amin * amin);
+                cls = (z2 >= (float)Tier<R>::z2_far) ? 2 : (z2 >= (float)Tier<R>::z2_fast) ? 1 : 0;
+            }
         }
-        if (fast) {
+        if (cls == 2) {
+            // K = 1: Av H = rho (k0 + rho (k1 + rho F2)), F2 = -2 G B Al, rho = 1/(dnu^2 + gamma^2);
+            // the K = 2 terms are below 4e-8 of a line's value here
+#pragma unroll 4
+            for (int i = 0; i < 32; ++i) {
+                const R b = tl.bhi[i], G = tl.G[i], k0 = tl.k0[i], k1 = tl.k[i].x, f2 = tl.f2[i];
+#pragma unroll
+                for (int g = 0; g < LS_G; ++g) {
+                    R d = pts.ohi[g] - b;
+                    R rho = rcp_fast(fma(d, d, G));
+                    R u = fma(fma(f2, rho, k1), rho, k0);
+                    acc[g] = fma(rho, u, acc[g]);
+                }
+            }
+        } else if (cls == 1) {
 #pragma unroll 2
             for (int i = 0; i < 32; ++i) {
                 const R b = tl.bhi[i], G = tl.G[i], k0 = tl.k0[i];
