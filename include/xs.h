@@ -37,7 +37,8 @@ typedef enum {
     XS_EUNSORTED = -2, /* line centres not ascending, or grid not strictly increasing */
     XS_ENOMEM = -3,    /* reserved for host-side allocation failure */
     XS_ECUDA = -4,     /* a CUDA launch or runtime call failed */
-    XS_ETIMEOUT = -5   /* a bounded host-side wait ran out */
+    XS_ETIMEOUT = -5,  /* a bounded host-side wait ran out */
+    XS_ETOOBIG = -6    /* the problem needs more scratch than xs_compute_noalloc's fixed array */
 } xs_status;
 
 typedef enum {
@@ -107,6 +108,31 @@ size_t xs_workspace_min_bytes(int64_t n_lines, int64_t N, int32_t L, int prec);
 int xs_compute(const xs_lines* lines, const double* nu, int64_t N, const double* T, const double* P_bar,
                int32_t L, double broad_scale, double wing_cut, int prec, void* sigma, void* workspace,
                size_t workspace_bytes, xs_stream stream);
+
+/*
+ * xs_compute without any allocation and without a caller workspace.
+ * (No counterpart in the paper: this is a deployment convenience.)
+ *
+ * For callers that cannot allocate device memory where they need a
+ * cross-section -- a host callback or real-time loop that must not block in the
+ * driver's allocator, a plugin whose host process owns and caps the memory pool,
+ * a tool that may only touch buffers it was handed.  Inputs, outputs and their
+ * meaning are exactly those of xs_compute; the scratch comes from a fixed 64 MiB
+ * device array inside libxs that every GPU loading the library holds until the
+ * process exits.  Problems whose smallest plan (one layer at a time) needs more
+ * than 64 MiB, i.e. xs_workspace_min_bytes(n, N, L, prec) > 64 MiB, are
+ * rejected with XS_ETOOBIG before any launch (roughly n * 44 bytes plus split-K
+ * partials of up to 64 * N * 8 bytes, at one layer per pass).
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture.  All calls on a device share the one array and
+ * every call overwrites it: calls whose execution overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Nothing in the array has to start at zero: each call writes every region
+ * before reading it.  Never calls cudaMalloc, cudaFree or any allocating routine.
+ */
+int xs_compute_noalloc(const xs_lines* lines, const double* nu, int64_t N, const double* T, const double* P_bar,
+                       int32_t L, double broad_scale, double wing_cut, int prec, void* sigma, xs_stream stream);
 
 /*
  * Reverse-mode adjoint of xs_compute.  Given g_sigma[n][j] = dF/dsigma[n][j]

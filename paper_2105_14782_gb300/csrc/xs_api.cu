@@ -134,6 +134,7 @@ const char* xs_strerror(int status)
     case XS_ENOMEM: return "out of host memory";
     case XS_ECUDA: return "CUDA error";
     case XS_ETIMEOUT: return "timed out";
+    case XS_ETOOBIG: return "problem exceeds the fixed scratch of xs_compute_noalloc";
     default: return "unknown status";
     }
 }
