@@ -256,6 +256,7 @@ namespace {
 struct ModelPlan {
     size_t T, vmr, sigma, dtau, F0, gF, gdtau, gsig, gvmr, gT, gTtmp, gb, xsws, emws, total;
     size_t xsws_bytes;
+    size_t xsws_sp[XS_MAX_SPECIES], xsws_sp_bytes[XS_MAX_SPECIES];
     int64_t max_nl;
 };
 
@@ -295,15 +296,21 @@ ModelPlan plan_model(const xs_model* m)
     p.gT = take(sizeof(double) * m->L);
     p.gTtmp = take(sizeof(double) * m->L);
     p.gb = take(sizeof(double) * Sp);
-    p.xsws_bytes = xs_workspace_bytes(p.max_nl, m->N, m->L, m->prec);
-    p.xsws = take(p.xsws_bytes);
+    // one full workspace per species, so the forward's line records stay valid
+    // for the adjoint of the same call
+    for (int s = 0; s < Sp; ++s) {
+        p.xsws_sp_bytes[s] = xs_workspace_bytes(m->species[s].n, m->N, m->L, m->prec);
+        p.xsws_sp[s] = take(p.xsws_sp_bytes[s]);
+    }
+    p.xsws_bytes = p.xsws_sp_bytes[0];
+    p.xsws = p.xsws_sp[0];
     p.emws = take(emission_workspace_bytes(m->L, m->N));
     p.total = off;
     return p;
 }
 
 int model_forward_impl(const xs_model* m, const double* theta, double* F0out, char* ws, const ModelPlan& p,
-                       cudaStream_t st)
+                       cudaStream_t st, int xs_flags = 0)
 {
     const int Sp = m->n_species;
     const size_t LN = (size_t)m->L * (size_t)m->N;
@@ -320,7 +327,8 @@ int model_forward_impl(const xs_model* m, const double* theta, double* F0out, ch
     for (int s = 0; s < Sp; ++s) {
         sp[s] = sig + es * LN * s;
         r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec,
-                        (void*)sp[s], ws + p.xsws, p.xsws_bytes, false, nullptr, nullptr, nullptr, st);
+                        (void*)sp[s], ws + p.xsws_sp[s], p.xsws_sp_bytes[s], false, nullptr, nullptr, nullptr, st,
+                        xs_flags);
         if (r) return r;
     }
     r = xsi::rt_tau(sp, Sp, vmr, m->P_bar, m->dP_bar, m->L, m->N, m->gravity, m->mu, m->kappa_coef, m->prec, dtau, st);
@@ -365,7 +373,7 @@ int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, doub
     const size_t LN = (size_t)m->L * (size_t)m->N;
     const size_t es = (m->prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
     double* F = F0 ? F0 : (double*)(ws + p.F0);
-    r = model_forward_impl(m, theta, F, ws, p, st);
+    r = model_forward_impl(m, theta, F, ws, p, st, xsi::XS_RUN_KEEP_ADJ);
     if (r) return r;
     double* T = (double*)(ws + p.T);
     double* vmr = (double*)(ws + p.vmr);
@@ -391,7 +399,7 @@ int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, doub
         return r;
     for (int s = 0; s < Sp; ++s) {
         r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec, nullptr,
-                        ws + p.xsws, p.xsws_bytes, true, gsp[s], gTtmp, gb + s, st);
+                        ws + p.xsws_sp[s], p.xsws_sp_bytes[s], true, gsp[s], gTtmp, gb + s, st, xsi::XS_RUN_REUSE);
         if (r) return r;
         if ((r = xsi::rt_accumulate(gT, gTtmp, m->L, 0, st))) return r;
     }

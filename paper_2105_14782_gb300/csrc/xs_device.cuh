@@ -53,7 +53,7 @@ template <> struct vec4<double> { using type = double4_32a; };
 template <class R> struct Tier;
 template <> struct Tier<float> {
     static constexpr float z2_fast = 625.0f;   // |z| >= 25: line-sum fast form (K = 2, real, per-line coefficients)
-    static constexpr float z2_fast_adj = 1600.0f; // |z| >= 40: adjoint fast form (K = 1; error < 2e-6 of a term)
+    static constexpr float z2_fast_adj = 625.0f; // |z| >= 25: adjoint fast form (K = 1; error < 6e-6 of a term)
     static constexpr float z2_far = 1.0e4f;    // |z| >= 100: K = 1 (closed real form)
     static constexpr float z2_mid1 = 625.0f;   // |z| >= 25 : K = 2
     static constexpr float z2_mid2 = 42.25f;   // |z| >= 6.5: K = 6, below: series

@@ -14,10 +14,13 @@ void count_launch(int n = 1);
 void prof_begin(int kind, cudaStream_t st);
 void prof_end(int kind, cudaStream_t st);
 
-// line-sum forward (adjoint == false: writes sigma) or adjoint (writes g_T, g_b)
+enum { XS_RUN_KEEP_ADJ = 1, XS_RUN_REUSE = 2 };
+
+// line-sum forward (adjoint == false: writes sigma) or adjoint (writes g_T, g_b);
+// flags as above (0 for a self-contained call)
 int xs_run(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L, double sb,
            double W, int prec, void* sigma, void* ws, size_t ws_bytes, bool adjoint, const double* g_sigma,
-           double* g_T, double* g_b, cudaStream_t st);
+           double* g_T, double* g_b, cudaStream_t st, int flags = 0);
 
 // checks ascending (grid == false: non-decreasing centres; grid == true: strictly
 // increasing grid) on the device; blocks on `st`; flag_dev is one device int

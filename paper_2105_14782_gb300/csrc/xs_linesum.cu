@@ -85,6 +85,48 @@ __global__ void layer_agg_init_kernel(float* agg, int n)
 //   rec2 = {c = 1/(sqrt2 beta), a = gamma c, Av = s c / sqrt(pi), Kc = K(a)}
 //   rec3 = {dlnS/dT, -n/T}                                                   (adjoint only)
 // s = S(T) * scale.  Per layer: agg[2n] = min c, agg[2n+1] = min a.
+// e^{-(k h)^2}, k = 1.., for the two series steps (h = 0.7f and h = 0.5)
+__device__ const float KC_E32[10] = {0.612626433f, 0.140858427f, 0.0121551799f, 0.00039366915f, 4.78511947e-06f,
+                                     2.18295906e-08f, 3.73757449e-11f, 2.40173736e-14f, 5.79232066e-18f,
+                                     5.24289428e-22f};
+__device__ const double KC_E64[13] = {0.77880078307140488, 0.36787944117144233, 0.10539922456186433,
+                                      0.018315638888734179, 0.0019304541362277093, 0.00012340980408667956,
+                                      4.7851173921290088e-06, 1.1253517471925912e-07, 1.6052280551856116e-09,
+                                      1.3887943864964021e-11, 7.2877240958196922e-14, 2.3195228302435691e-16,
+                                      4.4777324417183015e-19};
+
+// K(a) = erfcx(a) - (2 a h/pi) sum_k e^{-(kh)^2} / ((kh)^2 + a^2), the per-line constant
+// of the small-|z| series (see xs_device.cuh)
+__device__ __forceinline__ float series_K(float a)
+{
+    const float h = Tier<float>::h;
+    float s1 = 0.0f;
+#pragma unroll
+    for (int k = 1; k <= 10; ++k) {
+        float kh = (float)k * h;
+        s1 = fmaf(KC_E32[k - 1], rcp_fast(fmaf(kh, kh, a * a)), s1);
+    }
+    return erfcxf(a) - 2.0f * a * h * (float)(1.0 / PI) * s1;
+}
+__device__ __forceinline__ double series_K(double a)
+{
+    const double h = Tier<double>::h;
+    double s1 = 0.0;
+    for (int k = 1; k <= 13; ++k) {
+        double kh = k * h;
+        s1 += KC_E64[k - 1] / (kh * kh + a * a);
+    }
+    return erfcx(a) - 2.0 * a * h / PI * s1;
+}
+
+// Per (layer, line), rounded once to R:
+//   rec1 = {G = gamma^2, Al = s gamma/pi, F1 = 1.5 B Al, F2 = -2 G B Al}   (B = 2 beta^2)
+//   rec2 = {c = 1/(sqrt2 beta), a = gamma c, Av = s c / sqrt(pi), Kc = K(a)}
+//   clo  = c - (R)c,  rec3 = {dlnS/dT, -n/T} (adjoint only)
+// s = S(T) * scale.  The Boltzmann exponent of S (Eq. Slog) and c are formed in
+// FP64 in both paths; in the FP32 path the factors that only need ~1e-7
+// (stimulated emission, the width's temperature power, K(a)) use FP32.
+// Per layer: agg[2n] = min c, agg[2n+1] = min a.
 template <class R>
 __global__ void line_params_kernel(const double* __restrict__ nu_hat, const double* __restrict__ ln_S0,
                                    const double* __restrict__ elower, const double* __restrict__ gamma_ref,
@@ -98,51 +140,50 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
     int n = blockIdx.y;
     float cmin = __int_as_float(0x7f800000), amin = cmin;
     if (l < nl) {
-        double Tn = T[layer0 + n], Pn = P_bar[layer0 + n];
-        double nuh = nu_hat[l];
-        double lnTr = log(Tn / Tref);
-        // S(T) of Eq. Slog with Q(T)/Q(Tref) = (T/Tref)^q folded into one exponent
-        double S = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref) - qexp * lnTr) *
-                   (expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref));
-        double beta = sqrt(kB * Tn / (mass * amu)) * nuh / cL;
-        double gam = sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (Pn / bar_per_atm);
-        double s = S * scale;
-        double B = 2.0 * beta * beta, G = gam * gam;
-        double c = 1.0 / (SQRT2 * beta);
-        double a = gam * c;
-        double Al = s * gam / PI;
-        double Av = s * c * INV_SQRTPI;
-        double Kc = 0.0;
-        if (a * a < (double)Tier<R>::z2_mid2) {
-            const double h = (double)Tier<R>::h;
-            double s1 = 0.0;
-            const int kmax = (int)(6.3 / h) + 1; // e^{-(kh)^2} < 1e-17 beyond
-            for (int k = 1; k <= kmax; ++k) {
-                double kh = k * h;
-                s1 += exp(-kh * kh) / (kh * kh + a * a);
-            }
-            Kc = erfcx(a) - 2.0 * a * h / PI * s1;
+        const double Tn = T[layer0 + n], Pn = P_bar[layer0 + n];
+        const double nuh = nu_hat[l];
+        const double lnTr = log(Tn / Tref);
+        const double boltz = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref) - qexp * lnTr);
+        const double beta = sqrt(kB * Tn / (mass * amu)) * nuh / cL;
+        const double c = 1.0 / (SQRT2 * beta);
+        R stim, gam;
+        if (std::is_same<R, float>::value) {
+            const float u = (float)(c2 * nuh);
+            stim = (R)(expm1f(-u / (float)Tn) / expm1f(-u / (float)Tref));
+            gam = (R)((float)(sb * gamma_ref[l] * (Pn / bar_per_atm)) * expf(-(float)n_temp[l] * (float)lnTr));
+        } else {
+            stim = (R)(expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref));
+            gam = (R)(sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (Pn / bar_per_atm));
         }
-        size_t idx = (size_t)n * nl + l;
+        const double s = boltz * scale * (double)stim;
+        const R cr = (R)c;
+        const R a = gam * cr;
+        const R Al = (R)(s * (double)gam / PI);
+        const R Av = (R)(s * c * INV_SQRTPI);
+        const R B = R(1) / (cr * cr);
+        const R G = gam * gam;
+        const R Kc = (a * a < (R)Tier<R>::z2_mid2) ? series_K(a) : R(0);
+        const size_t idx = (size_t)n * nl + l;
         typename vec4<R>::type v1, v2;
-        v1.x = (R)G;
-        v1.y = (R)Al;
-        v1.z = (R)(1.5 * B * Al);
-        v1.w = (R)(-2.0 * G * B * Al);
-        v2.x = (R)c;
-        v2.y = (R)a;
-        v2.z = (R)Av;
-        v2.w = (R)Kc;
+        v1.x = G;
+        v1.y = Al;
+        v1.z = R(1.5) * B * Al;
+        v1.w = R(-2) * G * B * Al;
+        v2.x = cr;
+        v2.y = a;
+        v2.z = Av;
+        v2.w = Kc;
         rec1[idx] = v1;
         rec2[idx] = v2;
-        clo[idx] = (R)(c - (double)v2.x); // the part of c the rounded value misses
+        clo[idx] = (R)(c - (double)cr); // the part of c the rounded value misses
         if (rec3) {
-            double u = c2 * nuh / Tn;
-            double dlnS = c2 * elower[l] / (Tn * Tn) - qexp / Tn - (u / Tn) / expm1(u);
-            rec3[2 * idx] = (R)dlnS;
-            rec3[2 * idx + 1] = (R)(-n_temp[l] / Tn);
+            const R Tr = (R)Tn;
+            const R u = (R)(c2 * nuh) / Tr;
+            const R dlnS = (R)(c2 * elower[l] / (Tn * Tn) - qexp / Tn) - (u / Tr) / (R)expm1((double)u);
+            rec3[2 * idx] = dlnS;
+            rec3[2 * idx + 1] = (R)(-n_temp[l]) / Tr;
         }
-        cmin = (float)c * (1.0f - 1e-6f);
+        cmin = (float)cr * (1.0f - 1e-6f);
         amin = (float)a * (1.0f - 1e-6f);
     }
     // block min then one atomic per block (positive floats order like their bits)
@@ -638,10 +679,9 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                     for (int g = 0; g < LS_G; ++g) {
                         R d = pts.ohi[g] - b;
                         R rho = rcp_fast(fma(d, d, G));
-                        R ft = rho * fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x);
-                        R fb = rho * fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x);
-                        accT = fma(lam[g], ft, accT);
-                        accB = fma(lam[g], fb, accB);
+                        R lr = lam[g] * rho;
+                        accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
+                        accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
                     }
                 }
             } else {
@@ -662,11 +702,10 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                         for (int g = 0; g < LS_G; ++g) {
                             R d = pts.ohi[g] - bh;
                             R rho = rcp_fast(fma(d, d, G));
-                            R ft = rho * fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x);
-                            R fb = rho * fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x);
                             R lm = (full || (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y)) ? lam[g] : R(0);
-                            accT = fma(lm, ft, accT);
-                            accB = fma(lm, fb, accB);
+                            R lr = lm * rho;
+                            accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
+                            accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
                         }
                     } else {
                         const float bl = tl.blo[i];
@@ -679,6 +718,17 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                                 Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
                                 scaled_pair(dh, dl, p2.x, cl, &x, &xl);
                                 R a = p2.y;
+                                if (FAST && fma(x, x, a * a) >= (R)Tier<R>::z2_fast_adj) {
+                                    const R G = tl.G[i];
+                                    const R4 tc = tl.t[i];
+                                    const R4 uc = tl.u[i];
+                                    R d = dh + dl;
+                                    R rho = rcp_fast(fma(d, d, G));
+                                    R lr = lam[g] * rho;
+                                    accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
+                                    accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
+                                    continue;
+                                }
                                 R w4[4];
                                 voigt_w_dw<R>(x, xl, a, p2.w, w4);
                                 const R wr = w4[0], dr = w4[2], di = w4[3];
@@ -848,8 +898,13 @@ static int pick_plan(int64_t nl, int64_t N, int32_t L, int prec, size_t ws_bytes
 template <class R>
 static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L,
                   double sb, double W, void* sigma, char* ws, const XsPlan& p, bool adjoint,
-                  const double* g_sigma, double* g_T, double* g_b, cudaStream_t st)
+                  const double* g_sigma, double* g_T, double* g_b, cudaStream_t st, int flags)
 {
+    // flags: XS_RUN_KEEP_ADJ  (forward) also write the adjoint's per-line records
+    //        XS_RUN_REUSE     (adjoint) the records of an immediately preceding forward
+    //                         with the same inputs and workspace are still valid
+    const bool reuse = adjoint && (flags & XS_RUN_REUSE) && p.nchunks == 1;
+    const bool want_rec3 = adjoint || (flags & XS_RUN_KEEP_ADJ);
     using R4 = typename vec4<R>::type;
     const int64_t nl = ln->n;
     const bool mixed = (p.prec == XS_PREC_MIXED);
@@ -874,17 +929,21 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
         }
         return XS_OK;
     }
-    cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr);
-    layer_agg_init_kernel<<<(2 * L + 255) / 256, 256, 0, st>>>(agg, 2 * L);
-    count_launch(2);
+    if (!reuse) {
+        cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr);
+        layer_agg_init_kernel<<<(2 * L + 255) / 256, 256, 0, st>>>(agg, 2 * L);
+        count_launch(2);
+    }
     for (int c = 0; c < p.nchunks; ++c) {
         int l0 = c * p.Lc;
         int lc = std::min(p.Lc, L - l0);
-        dim3 pg((unsigned)((nl + 255) / 256), (unsigned)lc);
-        line_params_kernel<R><<<pg, 256, 0, st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp, nl,
-                                                   ln->mass_amu, ln->q_exponent, T, P, l0, sb, scale, rec1, rec2, clo,
-                                                   adjoint ? rec3 : nullptr, agg);
-        count_launch();
+        if (!reuse) {
+            dim3 pg((unsigned)((nl + 255) / 256), (unsigned)lc);
+            line_params_kernel<R><<<pg, 256, 0, st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp,
+                                                       nl, ln->mass_amu, ln->q_exponent, T, P, l0, sb, scale, rec1,
+                                                       rec2, clo, want_rec3 ? rec3 : nullptr, agg);
+            count_launch();
+        }
         dim3 grid((unsigned)strips, (unsigned)lc, (unsigned)p.ksplit);
         R4* r1b = rec1;
         R4* r2b = rec2;
@@ -918,13 +977,13 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
 
 int xs_run(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L, double sb,
            double W, int prec, void* sigma, void* ws, size_t ws_bytes, bool adjoint, const double* g_sigma,
-           double* g_T, double* g_b, cudaStream_t st)
+           double* g_T, double* g_b, cudaStream_t st, int flags)
 {
     XsPlan p;
     if (pick_plan(ln->n, N, L, prec, ws_bytes, &p) != XS_OK) return XS_EINVAL;
     if (prec == XS_PREC_FP64)
-        return run_xs<double>(ln, nu, N, T, P, L, sb, W, sigma, (char*)ws, p, adjoint, g_sigma, g_T, g_b, st);
-    return run_xs<float>(ln, nu, N, T, P, L, sb, W, sigma, (char*)ws, p, adjoint, g_sigma, g_T, g_b, st);
+        return run_xs<double>(ln, nu, N, T, P, L, sb, W, sigma, (char*)ws, p, adjoint, g_sigma, g_T, g_b, st, flags);
+    return run_xs<float>(ln, nu, N, T, P, L, sb, W, sigma, (char*)ws, p, adjoint, g_sigma, g_T, g_b, st, flags);
 }
 
 int check_sorted(const double* nu_hat, int64_t n, cudaStream_t st, int* flag_dev, bool grid)
