@@ -54,10 +54,11 @@ template <class R> struct Tier;
 template <> struct Tier<float> {
     static constexpr float z2_fast = 625.0f;   // |z| >= 25: line-sum fast form (K = 2, real, per-line coefficients)
     static constexpr float z2_fast_adj = 625.0f; // |z| >= 25: adjoint fast form (K = 1; error < 6e-6 of a term)
-    static constexpr float z2_far = 1.0e4f;    // |z| >= 100: K = 1 (closed real form)
-    static constexpr float z2_mid1 = 625.0f;   // |z| >= 25 : K = 2
+    static constexpr float z2_far = 625.0f;    // |z| >= 25 : K = 2
+    static constexpr float z2_mid1 = 100.0f;   // |z| >= 10 : K = 4
     static constexpr float z2_mid2 = 42.25f;   // |z| >= 6.5: K = 6, below: series
-    static constexpr int K1 = 1, K2 = 2, K3 = 6;
+    static constexpr float z2_series = 64.0f;  // the line sum uses the series below |z| = 8 (K = 5 form above)
+    static constexpr int K1 = 2, K2 = 4, K3 = 6;
     static constexpr float h = 0.7f;           // series step (error ~1e-8 relative)
     static constexpr int nwin = 8;             // E_n^- kept for |n - x/h| <= nwin
     static constexpr float tcut = 5.3f;        // E_n^+ kept while nh + x < tcut
@@ -68,6 +69,7 @@ template <> struct Tier<double> {
     static constexpr double z2_far = 22500.0;  // |z| >= 150: K = 3
     static constexpr double z2_mid1 = 1600.0;  // |z| >= 40 : K = 5
     static constexpr double z2_mid2 = 100.0;   // |z| >= 10 : K = 12, below: series
+    static constexpr double z2_series = 100.0;
     static constexpr int K1 = 3, K2 = 5, K3 = 12;
     static constexpr double h = 0.5;           // series step (error ~1e-17)
     static constexpr int nwin = 13;
@@ -226,8 +228,11 @@ __device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
 //   E_{n0+k} = E_{n0+k-1} e^{-2h delta} q^{2k-1},  E_{n0-k} = E_{n0-k+1} e^{+2h delta} q^{2k-1},
 //   q = e^{-h^2};
 // every factor has a small exponent, so no digits are lost to e^{-x^2} e^{2nhx}.
-// Terms with |k| > 6 are below 1e-9 of the peak term.
-__device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float Kc, float* wr, float* wi)
+// E_n^+ = E_n^- e^{-4nhx} rides along in the same loop.  Terms with |k| > 6 are
+// below 1e-9 of the peak term.  dtab[n-1] = 1/(n^2 h^2 + a^2) for n = 1..32
+// (one table per line, shared by the warp; nullptr: computed here).
+__device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float Kc, const float* dtab, float* wr,
+                                             float* wi)
 {
     const float h = Tier<float>::h;
     const int nw = 6;
@@ -240,65 +245,69 @@ __device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float 
     const float E0 = expf(-delta * delta);
     const float P = expf(-2.0f * h * delta);
     const float Pi = 1.0f / P;
+    // powers of R = e^{-4hx} for the E_n^+ = E_n^- R^n
+    const float R4 = expf(-4.0f * h * x);
+    const float R4i = 1.0f / R4;
+    float Rn = expf(-4.0f * h * x * (float)n0);
+    auto dn = [&](int n) -> float {
+        if (dtab != nullptr && n <= 32) return dtab[n - 1];
+        float nh = (float)n * h;
+        return rcp_fast(fmaf(nh, nh, a2));
+    };
     float sc = 0.0f, ss = 0.0f;
     if (n0 >= 1) {
-        float nh = (float)n0 * h;
-        float d = rcp_fast(fmaf(nh, nh, a2));
-        sc = d * E0;
-        ss = nh * d * E0;
+        float d = dn(n0);
+        float ep = E0 * Rn;
+        sc = d * (E0 + ep);
+        ss = (float)n0 * h * d * (E0 - ep);
     }
-    float Eu = E0, Ed = E0;
+    float Eu = E0, Ed = E0, Ru = Rn, Rd = Rn;
 #pragma unroll
     for (int k = 1; k <= nw; ++k) {
         Eu = Eu * P * Q[k - 1];
         Ed = Ed * Pi * Q[k - 1];
-        float nhu = (float)(n0 + k) * h;
-        float du = rcp_fast(fmaf(nhu, nhu, a2));
-        sc = fmaf(du, Eu, sc);
-        ss = fmaf(nhu * du, Eu, ss);
-        int nd = n0 - k;
+        Ru = Ru * R4;
+        Rd = Rd * R4i;
+        const int nu = n0 + k;
+        const float du = dn(nu);
+        const float epu = Eu * Ru;
+        sc = fmaf(du, Eu + epu, sc);
+        ss = fmaf((float)nu * h * du, Eu - epu, ss);
+        const int nd = n0 - k;
         if (nd >= 1) {
-            float nhd = (float)nd * h;
-            float dd = rcp_fast(fmaf(nhd, nhd, a2));
-            sc = fmaf(dd, Ed, sc);
-            ss = fmaf(nhd * dd, Ed, ss);
+            const float dd = dn(nd);
+            const float epd = Ed * Rd;
+            sc = fmaf(dd, Ed + epd, sc);
+            ss = fmaf((float)nd * h * dd, Ed - epd, ss);
         }
     }
-#pragma unroll 1
-    for (int n = 1; n <= 16; ++n) {
-        float nh = (float)n * h;
-        float t = (nh + xh) + xl;
-        if (!(t < Tier<float>::tcut)) break;
-        float e = expf(-t * t);
-        float d = rcp_fast(fmaf(nh, nh, a2));
-        sc = fmaf(d, e, sc);
-        ss = fmaf(-nh * d, e, ss);
-    }
     float ex = exp_negsq(xh) * (1.0f - 2.0f * xh * xl);
-    float s2, c2v;
-    sincosf(2.0f * a * x, &s2, &c2v);
-    float sax = sinf(a * x);
+    float sax, cax;
+    sincosf(a * x, &sax, &cax);
+    const float c2v = 1.0f - 2.0f * sax * sax; // cos 2ax
+    const float s2 = 2.0f * sax * cax;         // sin 2ax
     float sax_a = (a > 0.0f) ? sax / a : x;
-    float s2_a = (a > 0.0f) ? s2 / a : 2.0f * x;
+    float s2_a = 2.0f * sax_a * cax;
     const float hpi = h * (float)(1.0 / PI);
     *wr = ex * (Kc * c2v + 2.0f * hpi * sax * sax_a) + a * hpi * sc;
     *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
 }
 
 template <class R>
-__device__ __forceinline__ void w_small(R x, R xl, R a, R Kc, R* wr, R* wi)
+__device__ __forceinline__ void w_small(R x, R xl, R a, R Kc, const R*, R* wr, R* wi)
 {
     w_series<R>(x, xl, a, Kc, wr, wi);
 }
 template <>
-__device__ __forceinline__ void w_small<float>(float x, float xl, float a, float Kc, float* wr, float* wi)
+__device__ __forceinline__ void w_small<float>(float x, float xl, float a, float Kc, const float* dtab, float* wr,
+                                               float* wi)
 {
-    w_series_rec(x, xl, a, Kc, wr, wi);
+    w_series_rec(x, xl, a, Kc, dtab, wr, wi);
 }
 
-// w(x + ia) for any tier; x = x + xl >= 0.
+// w(x + ia) for any tier; x = x + xl >= 0; dtab: see w_series_rec (may be nullptr).
 template <class R>
-__device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
+__device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi, const R* dtab = nullptr)
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
@@ -310,13 +319,13 @@ __device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi)
         else
             w_asym<R, Tier<R>::K3>(x, a, r, wr, wi);
     } else {
-        w_small<R>(x, xl, a, Kc, wr, wi);
+        w_small<R>(x, xl, a, Kc, dtab, wr, wi);
     }
 }
 
 // w and w' for any tier; x = x + xl >= 0.
 template <class R>
-__device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R* dr, R* di)
+__device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R* dr, R* di, const R* dtab = nullptr)
 {
     R z2 = fma(x, x, a * a);
     if (z2 >= Tier<R>::z2_mid2) {
@@ -332,7 +341,7 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
             dw_asym<R, Tier<R>::K3>(x, a, r, dr, di);
         }
     } else {
-        w_small<R>(x, xl, a, Kc, wr, wi);
+        w_small<R>(x, xl, a, Kc, dtab, wr, wi);
         // w' = -2 z w + 2i/sqrt(pi)
         *dr = R(-2) * (x * *wr - a * *wi);
         *di = R(-2) * (x * *wi + a * *wr) + R(2 * INV_SQRTPI);
@@ -341,17 +350,51 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
 
 // Out-of-line entry points for the per-point tiered evaluation, so the hot
 // loops that call them stay small in the instruction cache.
+// Series-only entry (FP32 line sum, |z| < 8): Re w.
+static __device__ __noinline__ float voigt_H_series(float x, float xl, float a, float Kc, const float* dtab)
+{
+    float wr, wi;
+    w_series_rec(x, xl, a, Kc, dtab, &wr, &wi);
+    return wr;
+}
+
+// Asymptotic series of Eq. asywofz truncated at K = 5, in real form:
+//   Re w = (a r / sqrt(pi)) sum_{k<=5} sum_{m<=k} W5[k][m] r^k t^m,  r = 1/|z|^2, t = a^2 r,
+// W5[k][m] = c_k q_{k,m} with c_k = (2k-1)!!/2^k and q_k(t) = Im((x+ia)^{2k+1}) / (a |z|^{2k}).
+// Truncation error below 4e-8 of Re w for |z| >= 8.
+__device__ const float W5[6][6] = {{1.0f, 0, 0, 0, 0, 0},
+                                   {1.5f, -2.0f, 0, 0, 0, 0},
+                                   {3.75f, -15.0f, 12.0f, 0, 0, 0},
+                                   {13.125f, -105.0f, 210.0f, -120.0f, 0, 0},
+                                   {59.0625f, -787.5f, 2835.0f, -3780.0f, 1680.0f, 0},
+                                   {324.84375f, -6496.875f, 36382.5f, -83160.0f, 83160.0f, -30240.0f}};
+
+// Coefficient n (0..10) of the same sum written in rho = 1/(dnu^2 + gamma^2) for one line:
+//   Av H = rho sum_n C_n rho^n,  C_n = Al sum_{k+m=n} W5[k][m] B^k G^m   (B = 2 beta^2, G = gamma^2)
+__device__ __forceinline__ float k5_coeff(int n, float Al, float B, float G)
+{
+    float c = 0.0f;
+    for (int k = (n + 1) / 2; k <= (n < 5 ? n : 5); ++k) {
+        const int m = n - k;
+        float bk = 1.0f, gm = 1.0f;
+        for (int i = 0; i < k; ++i) bk *= B;
+        for (int i = 0; i < m; ++i) gm *= G;
+        c = fmaf(W5[k][m], bk * gm, c);
+    }
+    return Al * c;
+}
+
 template <class R>
-__device__ __noinline__ R voigt_H(R x, R xl, R a, R Kc)
+__device__ __noinline__ R voigt_H(R x, R xl, R a, R Kc, const R* dtab)
 {
     R wr, wi;
-    faddeeva<R>(x, xl, a, Kc, &wr, &wi);
+    faddeeva<R>(x, xl, a, Kc, &wr, &wi, dtab);
     return wr;
 }
 template <class R>
-__device__ __noinline__ void voigt_w_dw(R x, R xl, R a, R Kc, R* w4)
+__device__ __noinline__ void voigt_w_dw(R x, R xl, R a, R Kc, R* w4, const R* dtab)
 {
-    faddeeva_d<R>(x, xl, a, Kc, &w4[0], &w4[1], &w4[2], &w4[3]);
+    faddeeva_d<R>(x, xl, a, Kc, &w4[0], &w4[1], &w4[2], &w4[3], dtab);
 }
 
 } // namespace xsd

@@ -162,7 +162,7 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
         const R Av = (R)(s * c * INV_SQRTPI);
         const R B = R(1) / (cr * cr);
         const R G = gam * gam;
-        const R Kc = (a * a < (R)Tier<R>::z2_mid2) ? series_K(a) : R(0);
+        const R Kc = (a * a < (R)Tier<R>::z2_series) ? series_K(a) : R(0);
         const size_t idx = (size_t)n * nl + l;
         typename vec4<R>::type v1, v2;
         v1.x = G;
@@ -322,7 +322,101 @@ struct LineTile {
     typename vec4<R>::type r2[32];
     R clo[32];
     int2 jr[32];
+    // the fast-form constants again, each duplicated so that one broadcast load
+    // fills a register pair for the packed two-point FP32 instructions:
+    float4 q0[32]; // (-b, -b, G, G)
+    float4 q1[32]; // (k0, k0, k1, k1)
+    float4 q2[32]; // (k2, k2, k3, k3)
+    float4 q3[32]; // (k4, k4, F2, F2)
 };
+
+// Packed fast forms: two grid points per FP32 instruction (FADD2/FFMA2), one
+// reciprocal each.  Only the FP32 path has them; the FP64 path never takes a
+// fast branch.
+template <class R>
+__device__ __forceinline__ void fast_k1(const LineTile<R>&, const R (&)[LS_G], R (&)[LS_G])
+{
+}
+template <class R>
+__device__ __forceinline__ void fast_k2(const LineTile<R>&, const R (&)[LS_G], R (&)[LS_G])
+{
+}
+
+__device__ __forceinline__ float2 f2lo(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 f2hi(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(rcp_fast(v.x), rcp_fast(v.y)); }
+// both reciprocals from one: 1/D1 = D2/(D1 D2), 1/D2 = D1/(D1 D2) (about 1.5 ulp);
+// trades a second MUFU op for two FP32 multiplies.  D1 D2 stays in range in the fast
+// forms (0.01 < D < 1e4 there).
+__device__ __forceinline__ float2 rcp2_shared(float2 v)
+{
+    float r = rcp_fast(v.x * v.y);
+    return __fmul2_rn(make_float2(v.y, v.x), make_float2(r, r));
+}
+// pairs 0 and 1 share one reciprocal, pairs 2 and 3 take one each: this balances
+// the MUFU pipe (16 ops/clk/SM) against the FP32 pipe (128 lanes/clk/SM)
+__device__ __forceinline__ float2 rcp2_mix(float2 v, int p) { return (p < 2) ? rcp2_shared(v) : rcp2(v); }
+
+// K = 1: acc += rho (k0 + rho (k1 + rho F2)),  rho = 1/((o - b)^2 + G)
+template <>
+__device__ __forceinline__ void fast_k1<float>(const LineTile<float>& tl, const float (&ohi)[LS_G],
+                                               float (&acc)[LS_G])
+{
+    float2 o2[LS_G / 2], a2[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
+        a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
+    }
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v3 = tl.q3[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), f2 = f2hi(v3);
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
+            float2 u = __ffma2_rn(__ffma2_rn(f2, rho, k1), rho, k0);
+            a2[p] = __ffma2_rn(rho, u, a2[p]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        acc[2 * p] = a2[p].x;
+        acc[2 * p + 1] = a2[p].y;
+    }
+}
+
+// K = 2: acc += rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
+template <>
+__device__ __forceinline__ void fast_k2<float>(const LineTile<float>& tl, const float (&ohi)[LS_G],
+                                               float (&acc)[LS_G])
+{
+    float2 o2[LS_G / 2], a2[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
+        a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
+    }
+#pragma unroll 2
+    for (int i = 0; i < 32; ++i) {
+        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v2 = tl.q2[i], v3 = tl.q3[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), k2 = f2lo(v2), k3 = f2hi(v2),
+                     k4 = f2lo(v3);
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
+            float2 u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(k4, rho, k3), rho, k2), rho, k1), rho, k0);
+            a2[p] = __ffma2_rn(rho, u, a2[p]);
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        acc[2 * p] = a2[p].x;
+        acc[2 * p + 1] = a2[p].y;
+    }
+}
 
 // Fast form of a line's term from the asymptotic series with K = 2 (Eq. asywofz),
 // written in rho = 1/(dnu^2 + gamma^2):  Av H = rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
@@ -342,6 +436,156 @@ __device__ __forceinline__ void fast_coeffs(const typename vec4<R>::type& p1, R 
 }
 
 // one lane's line record as loaded from global memory
+// ---- mixed chunks (FP32 only): per-line dispatch with packed arithmetic
+
+// K = 2 form over lines [i0, i1) of the tile; when masked, each point only takes
+// the lines whose cut range holds it.
+__device__ __forceinline__ void k2_lines(const LineTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
+                                         float2 (&a2)[LS_G / 2], bool masked, const int (&jg)[LS_G])
+{
+    for (int i = i0; i < i1; ++i) {
+        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v2 = tl.q2[i], v3 = tl.q3[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), k2 = f2lo(v2), k3 = f2hi(v2),
+                     k4 = f2lo(v3);
+        const int2 jr = tl.jr[i];
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
+            float2 u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(k4, rho, k3), rho, k2), rho, k1), rho, k0);
+            if (masked) {
+                rho.x = (jg[2 * p] >= jr.x && jg[2 * p] <= jr.y) ? rho.x : 0.0f;
+                rho.y = (jg[2 * p + 1] >= jr.x && jg[2 * p + 1] <= jr.y) ? rho.y : 0.0f;
+            }
+            a2[p] = __ffma2_rn(rho, u, a2[p]);
+        }
+    }
+}
+
+// One line near the warp's points: the K = 5 form in rho (coefficients ctab[0..10],
+// see k5_coeff) at every point with |z| >= 8, i.e. dnu^2 >= dthr2, and the small-|z|
+// series (dtab, see w_series_rec) at the others.
+__device__ __forceinline__ void near_line(const LineTile<float>& tl, int i, const float (&ohi)[LS_G],
+                                          const float* olo, const float* ctab, const float* dtab,
+                                          float2 (&a2)[LS_G / 2], const int (&jg)[LS_G])
+{
+    const int lane = threadIdx.x & 31;
+    const float bh = tl.bhi[i], bl = tl.blo[i], G = tl.G[i], cl = tl.clo[i];
+    const float4 p2 = tl.r2[i];
+    const int2 jr = tl.jr[i];
+    const float a = p2.y, c = p2.x;
+    const float dthr2 = fmaxf(Tier<float>::z2_series - a * a, 0.0f) * rcp_fast(c * c);
+    float dh[LS_G], dl[LS_G];
+    float2 rho[LS_G / 2], u[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = 2 * p + q;
+            dh[g] = ohi[g] - bh;
+            dl[g] = olo[g * 32 + lane] - bl;
+        }
+        float2 d = __fadd2_rn(make_float2(dh[2 * p], dh[2 * p + 1]), make_float2(dl[2 * p], dl[2 * p + 1]));
+        rho[p] = rcp2(__ffma2_rn(d, d, make_float2(G, G)));
+        const float cc = ctab[10];
+        u[p] = make_float2(cc, cc);
+    }
+#pragma unroll
+    for (int n = 9; n >= 0; --n) {
+        const float cc = ctab[n];
+        const float2 c2 = make_float2(cc, cc);
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) u[p] = __ffma2_rn(u[p], rho[p], c2);
+    }
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        float2 v = __fmul2_rn(rho[p], u[p]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int g = 2 * p + q;
+            const float d = dh[g] + dl[g];
+            const bool in = jg[g] >= jr.x && jg[g] <= jr.y;
+            float add = (q == 0) ? v.x : v.y;
+            if (!(in && d * d >= dthr2)) add = 0.0f;
+            if (__any_sync(0xffffffffu, in && d * d < dthr2)) {
+                if (in && d * d < dthr2) {
+                    float x, xl;
+                    scaled_pair(dh[g], dl[g], c, cl, &x, &xl);
+                    add = p2.z * voigt_H_series(x, xl, a, p2.w, dtab);
+                }
+            }
+            if (q == 0) a2[p].x += add; else a2[p].y += add;
+        }
+    }
+}
+
+// Whole mixed chunk: runs of lines that are far (|z| >= 25 at every point) and
+// cover the warp go through the packed K = 2 loop; far lines that cover only part
+// of the warp take it masked; the rest go through near_line.
+__device__ __forceinline__ void mixed_chunk(const LineTile<float>& tl, const WarpPoints<float>& pts,
+                                            const float* olo, float* ctab, float* dtab, float (&acc)[LS_G])
+{
+    const int lane = threadIdx.x & 31;
+    // classify line `lane`
+    const float bh = tl.bhi[lane];
+    const float4 p2 = tl.r2[lane];
+    const int2 jr = tl.jr[lane];
+    const float dist = fmaxf(fmaxf(bh - pts.ow1, pts.ow0 - bh), 0.0f);
+    const float xm = dist * p2.x;
+    const bool far = fmaf(xm, xm, p2.y * p2.y) >= Tier<float>::z2_fast;
+    const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
+    const unsigned fm = __ballot_sync(0xffffffffu, far && full);
+    const unsigned em = __ballot_sync(0xffffffffu, far && !full);
+
+    float2 o2[LS_G / 2], a2[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        o2[p] = make_float2(pts.ohi[2 * p], pts.ohi[2 * p + 1]);
+        a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
+    }
+    int i = 0;
+    while (i < 32) {
+        const unsigned rest = fm >> i;
+        if (rest & 1u) {
+            const unsigned zeros = ~rest;
+            const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
+            k2_lines(tl, i, j, o2, a2, false, pts.jg);
+            i = j;
+        } else if ((em >> i) & 1u) {
+            k2_lines(tl, i, i + 1, o2, a2, true, pts.jg);
+            ++i;
+        } else {
+            // per-line tables shared by the warp
+            const float4 q = tl.r2[i];
+            const float hn = (float)(lane + 1) * Tier<float>::h;
+            __syncwarp();
+            dtab[lane] = rcp_fast(fmaf(hn, hn, q.y * q.y));
+            if (lane < 11) ctab[lane] = k5_coeff(lane, tl.k0[i], rcp_fast(q.x * q.x), tl.G[i]);
+            __syncwarp();
+            near_line(tl, i, pts.ohi, olo, ctab, dtab, a2, pts.jg);
+            ++i;
+        }
+    }
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        acc[2 * p] = a2[p].x;
+        acc[2 * p + 1] = a2[p].y;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void mixed_chunk_dispatch(const LineTile<R>&, const WarpPoints<R>&, const float*, float*,
+                                                     float*, R (&)[LS_G])
+{
+}
+template <>
+__device__ __forceinline__ void mixed_chunk_dispatch<float>(const LineTile<float>& tl, const WarpPoints<float>& pts,
+                                                            const float* olo, float* ctab, float* dtab,
+                                                            float (&acc)[LS_G])
+{
+    mixed_chunk(tl, pts, olo, ctab, dtab, acc);
+}
+
 template <class R>
 struct LineRec {
     double nu;
@@ -381,12 +625,16 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     using R4 = typename vec4<R>::type;
     __shared__ LineTile<R> tiles[LS_WARPS];
     __shared__ float olo_s[LS_WARPS][32 * LS_G];
+    __shared__ R dtab_s[LS_WARPS][32];
+    __shared__ float ctab_s[LS_WARPS][12];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
     const int64_t j0 = (int64_t)strip * LS_STRIP;
     const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
     LineTile<R>& tl = tiles[w];
     float* olo = olo_s[w];
+    R* dtab = dtab_s[w];
+    float* ctab = ctab_s[w];
 
     WarpPoints<R> pts;
     if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast, olo)) return;
@@ -426,6 +674,13 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
             tl.r2[lane] = nx.p2;
             tl.clo[lane] = nx.cl;
             tl.jr[lane] = nx.jr;
+            if (FAST) {
+                const float nbf = -(float)bh, Gf = (float)nx.p1.x;
+                tl.q0[lane] = make_float4(nbf, nbf, Gf, Gf);
+                tl.q1[lane] = make_float4((float)k0, (float)k0, (float)kk.x, (float)kk.x);
+                tl.q2[lane] = make_float4((float)kk.y, (float)kk.y, (float)kk.z, (float)kk.z);
+                tl.q3[lane] = make_float4((float)kk.w, (float)kk.w, (float)nx.p1.w, (float)nx.p1.w);
+            }
         }
         __syncwarp();
         if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, t0 + 32 + lane, ce); // in flight meanwhile
@@ -445,32 +700,13 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
         if (cls == 2) {
             // K = 1: Av H = rho (k0 + rho (k1 + rho F2)), F2 = -2 G B Al, rho = 1/(dnu^2 + gamma^2);
             // the K = 2 terms are below 4e-8 of a line's value here
-#pragma unroll 4
-            for (int i = 0; i < 32; ++i) {
-                const R b = tl.bhi[i], G = tl.G[i], k0 = tl.k0[i], k1 = tl.k[i].x, f2 = tl.f2[i];
-#pragma unroll
-                for (int g = 0; g < LS_G; ++g) {
-                    R d = pts.ohi[g] - b;
-                    R rho = rcp_fast(fma(d, d, G));
-                    R u = fma(fma(f2, rho, k1), rho, k0);
-                    acc[g] = fma(rho, u, acc[g]);
-                }
-            }
+            fast_k1<R>(tl, pts.ohi, acc);
         } else if (cls == 1) {
-#pragma unroll 2
-            for (int i = 0; i < 32; ++i) {
-                const R b = tl.bhi[i], G = tl.G[i], k0 = tl.k0[i];
-                const R4 k = tl.k[i];
-#pragma unroll
-                for (int g = 0; g < LS_G; ++g) {
-                    R d = pts.ohi[g] - b;
-                    R rho = rcp_fast(fma(d, d, G));
-                    R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
-                    acc[g] = fma(rho, u, acc[g]);
-                }
-            }
+            fast_k2<R>(tl, pts.ohi, acc);
+        } else if (FAST) {
+            mixed_chunk_dispatch<R>(tl, pts, olo, ctab, (float*)dtab, acc);
         } else {
-            // Per line (warp-uniform): if every point of the warp is at |z| >= 100
+            // FP64: per line (warp-uniform): if every point of the warp is at |z| >= 100
             // use the Lorentz-wing form, masked by the cut only when the line does
             // not cover the whole warp; else choose the Faddeeva tier per point.
             for (int i = 0; i < 32; ++i) {
@@ -496,19 +732,36 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
                 } else {
                     const float bl = tl.blo[i];
                     const R cl = tl.clo[i];
+                    if (FAST) {
+                        // per line, shared by the warp: 1/(n^2 h^2 + a^2) (n = 1..32) for the
+                        // small-|z| series, and the 11 coefficients of the K = 5 form in rho
+                        const R hn = R(lane + 1) * (R)Tier<R>::h;
+                        __syncwarp();
+                        dtab[lane] = rcp_fast(fma(hn, hn, p2.y * p2.y));
+                        if (lane < 11) ctab[lane] = k5_coeff(lane, (float)k0, (float)rcp_fast(p2.x * p2.x), (float)G);
+                        __syncwarp();
+                    }
 #pragma unroll
                     for (int g = 0; g < LS_G; ++g) {
                         if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
                             R dh, dl, x, xl;
                             Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
                             scaled_pair(dh, dl, p2.x, cl, &x, &xl);
-                            if (FAST && fma(x, x, p2.y * p2.y) >= (R)Tier<R>::z2_fast) {
+                            const R z2 = fma(x, x, p2.y * p2.y);
+                            if (FAST && z2 >= (R)Tier<R>::z2_series) {
+                                // |z| >= 8: K = 5 asymptotic form, uniform across the warp
                                 R d = dh + dl;
                                 R rho = rcp_fast(fma(d, d, G));
-                                R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
+                                R u = (R)ctab[10];
+#pragma unroll
+                                for (int n = 9; n >= 0; --n) u = fma(u, rho, (R)ctab[n]);
                                 acc[g] = fma(rho, u, acc[g]);
+                            } else if (FAST) {
+                                acc[g] = fma(p2.z, (R)voigt_H_series((float)x, (float)xl, (float)p2.y, (float)p2.w,
+                                                                     (const float*)dtab),
+                                             acc[g]);
                             } else {
-                                acc[g] = fma(p2.z, voigt_H<R>(x, xl, p2.y, p2.w), acc[g]);
+                                acc[g] = fma(p2.z, voigt_H<R>(x, xl, p2.y, p2.w, nullptr), acc[g]);
                             }
                         }
                     }
@@ -572,7 +825,46 @@ struct AdjTile {
     typename vec4<R>::type u[32]; // fast form: f_b = rho (U1 + rho (U2 + rho (U3 + rho U4)))
     R G[32], clo[32], aS[32], nn[32];
     int2 jr[32];
+    // duplicated constants for the packed fast form (FP32 path only)
+    float4 q0[32];           // (-b, -b, G, G)
+    float4 qt0[32], qt1[32]; // (T1, T1, T2, T2), (T3, T3, T4, T4)
+    float4 qu0[32], qu1[32]; // (U1, U1, U2, U2), (U3, U3, U4, U4)
 };
+
+template <class R>
+__device__ __forceinline__ void fast_adj(const AdjTile<R>&, const R (&)[LS_G], const R (&)[LS_G], R&, R&)
+{
+}
+// lambda rho P_T(rho) and lambda rho P_U(rho), two points per packed instruction
+template <>
+__device__ __forceinline__ void fast_adj<float>(const AdjTile<float>& tl, const float (&ohi)[LS_G],
+                                                const float (&lam)[LS_G], float& accT, float& accB)
+{
+    float2 o2[LS_G / 2], l2[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
+        l2[p] = make_float2(lam[2 * p], lam[2 * p + 1]);
+    }
+    float2 aT = make_float2(accT, 0.0f), aB = make_float2(accB, 0.0f);
+#pragma unroll 2
+    for (int i = 0; i < 32; ++i) {
+        const float4 v0 = tl.q0[i], t0 = tl.qt0[i], t1 = tl.qt1[i], u0 = tl.qu0[i], u1 = tl.qu1[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0);
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2(__ffma2_rn(d, d, G));
+            float2 lr = __fmul2_rn(l2[p], rho);
+            float2 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
+            float2 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
+            aT = __ffma2_rn(lr, pt, aT);
+            aB = __ffma2_rn(lr, pu, aB);
+        }
+    }
+    accT = aT.x + aT.y;
+    accB = aB.x + aB.y;
+}
 
 // Per evaluation the adjoint accumulates
 //   f_T = (dlnS/dT) V0 + (1/(2T)) D_beta + (-n/T) D_gamma   and   f_b = D_gamma
@@ -593,6 +885,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     using R4 = typename vec4<R>::type;
     __shared__ AdjTile<R> tiles[LS_WARPS];
     __shared__ float olo_s[LS_WARPS][32 * LS_G];
+    __shared__ R dtab_s[LS_WARPS][32];
     __shared__ double red[2][LS_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
@@ -654,6 +947,14 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                 tl.G[lane] = G;
                 tl.aS[lane] = aS;
                 tl.nn[lane] = nn;
+                if (FAST) {
+                    const float nbf = -(float)bh, Gf = (float)G;
+                    tl.q0[lane] = make_float4(nbf, nbf, Gf, Gf);
+                    tl.qt0[lane] = make_float4((float)tc.x, (float)tc.x, (float)tc.y, (float)tc.y);
+                    tl.qt1[lane] = make_float4((float)tc.z, (float)tc.z, (float)tc.w, (float)tc.w);
+                    tl.qu0[lane] = make_float4((float)uc.x, (float)uc.x, (float)uc.y, (float)uc.y);
+                    tl.qu1[lane] = make_float4((float)uc.z, (float)uc.z, (float)uc.w, (float)uc.w);
+                }
             }
             __syncwarp();
             if (t0 + 32 < ce) {
@@ -669,21 +970,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                                         amin, (float)Tier<R>::z2_fast_adj);
             }
             if (fast) {
-#pragma unroll 2
-                for (int i = 0; i < 32; ++i) {
-                    const R b = tl.bhi[i];
-                    const R G = tl.G[i];
-                    const R4 tc = tl.t[i];
-                    const R4 uc = tl.u[i];
-#pragma unroll
-                    for (int g = 0; g < LS_G; ++g) {
-                        R d = pts.ohi[g] - b;
-                        R rho = rcp_fast(fma(d, d, G));
-                        R lr = lam[g] * rho;
-                        accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
-                        accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
-                    }
-                }
+                fast_adj<R>(tl, pts.ohi, lam, accT, accB);
             } else {
                 for (int i = 0; i < 32; ++i) {
                     const R bh = tl.bhi[i];
@@ -711,6 +998,13 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                         const float bl = tl.blo[i];
                         const R cl = tl.clo[i];
                         const R aS = tl.aS[i], nn = tl.nn[i];
+                        R* dtab = dtab_s[w];
+                        if (FAST) {
+                            const R hn = R(lane + 1) * (R)Tier<R>::h;
+                            __syncwarp();
+                            dtab[lane] = rcp_fast(fma(hn, hn, p2.y * p2.y));
+                            __syncwarp();
+                        }
 #pragma unroll
                         for (int g = 0; g < LS_G; ++g) {
                             if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
@@ -730,7 +1024,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                                     continue;
                                 }
                                 R w4[4];
-                                voigt_w_dw<R>(x, xl, a, p2.w, w4);
+                                voigt_w_dw<R>(x, xl, a, p2.w, w4, FAST ? dtab : nullptr);
                                 const R wr = w4[0], dr = w4[2], di = w4[3];
                                 // H_x = Re w', H_a = -Im w'
                                 R V0 = p2.z * wr;
