@@ -2,22 +2,28 @@
 // direct line-profile sum (Eq. crosssec summed over lines, Sec. 3.1) and its
 // reverse-mode adjoint.
 //
-// Work decomposition.  Lines are sorted by centre.  A CTA owns one strip of
-// STRIP = 1024 consecutive grid points of one layer; each of its 4 warps owns
-// 256 points (G = 8 per lane, lane-interleaved) and walks the strip's line window
-// (all lines with an in-cut point in the strip, optionally split into K chunks
-// across CTAs).  Lines are staged through shared memory 128 at a time and every
-// warp reads them as broadcasts.  For each 32-line sub-tile a warp decides once
-// whether all its points are inside every line's wing cut and at |z| >= 100;
-// then the whole sub-tile runs the 5-FP32-op + 1-reciprocal Lorentz-wing form
-// of the asymptotic Faddeeva series (the bulk of the work).  Otherwise each
-// evaluation checks the cut by integer index and picks its Faddeeva tier.
+// Partition.  For every (layer, line) the grid points inside the wing cut are
+// split, in FP64, into the line's "near" index range (|z| < 25, z = x + ia) and
+// the rest.  The far part (about 98% of the evaluations) is summed by the main
+// kernels with the Lorentz-wing forms of the asymptotic series (Eq. asywofz) in
+// packed FP32x2 arithmetic; the near part by the near kernels, one thread per
+// grid point, with the full tiered Faddeeva function (xs_device.cuh).  Both use
+// the same integer ranges, so every (line, point) pair is counted exactly once.
+//
+// Main kernels.  Lines are sorted by centre.  A CTA owns one strip of 1,024
+// consecutive grid points of one layer; each of its 4 warps owns 256 points
+// (8 per lane, lane-interleaved) and walks the strip's line window (all lines
+// with an in-cut point in the strip, optionally split into K chunks across CTAs)
+// in 32-line chunks it stages itself in shared memory.  A chunk whose lines all
+// cover the warp's points with no near point runs unmasked (K = 1 form when
+// every pair is at |z| >= 100, else K = 2); other chunks mask per (line, point).
 //
 // Precision (XS_PREC_MIXED): per-line scalars are formed in FP64 and rounded
-// once; the line-centre offset nu_j - nu_hat is formed from FP64 offsets to the
-// strip's reference point (hi + lo floats); Voigt values and sums are FP32, with
-// the running sum per grid point kept as an FP32 (hi, lo) pair updated after
-// every 32 lines (Fast2Sum).  XS_PREC_FP64 runs the same code in double.
+// once; line-centre offsets are formed in FP64 relative to the warp's middle
+// grid point and rounded to float (hi + lo where it matters); Voigt values and
+// sums are FP32, with each point's running sum an FP32 (hi, lo) pair updated by
+// TwoSum after every 32 lines.  XS_PREC_FP64 has no fast forms and no near split:
+// every pair goes through the double-precision tiered Faddeeva function.
 #include <algorithm>
 #include <type_traits>
 
@@ -33,6 +39,8 @@ constexpr int LS_STRIP = LS_WARPS * 32 * LS_G; // 1024
 // resident CTAs per SM the register budget targets (FP32: 96 registers; FP64 keeps more)
 template <class R> struct MinBlocks { static constexpr int v = 5; };
 template <> struct MinBlocks<double> { static constexpr int v = 3; };
+// the near/far boundary of the FP32 path: pairs at |z| < NEAR_Z go to the near kernels
+constexpr double NEAR_Z = 25.0;
 
 // ------------------------------------------------------------------ K0: cut ranges
 
@@ -134,7 +142,8 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
                                    const double* __restrict__ T, const double* __restrict__ P_bar, int layer0,
                                    double sb, double scale, typename vec4<R>::type* __restrict__ rec1,
                                    typename vec4<R>::type* __restrict__ rec2, R* __restrict__ clo,
-                                   R* __restrict__ rec3, float* __restrict__ agg)
+                                   R* __restrict__ rec3, float* __restrict__ agg, const double* __restrict__ nu,
+                                   int64_t N, const int2* __restrict__ jrange, int2* __restrict__ jnear)
 {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = blockIdx.y;
@@ -183,6 +192,31 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
             rec3[2 * idx] = dlnS;
             rec3[2 * idx + 1] = (R)(-n_temp[l]) / Tr;
         }
+        if (jnear) {
+            // near range: in-cut points with |nu_j - nu_hat| < sqrt(625 - a^2)/c, i.e. |z| < 25
+            const double ad = gam * c;
+            const double lim = (double)NEAR_Z * NEAR_Z - ad * ad;
+            int2 r = make_int2(1, 0); // empty
+            if (lim > 0.0) {
+                const double del = sqrt(lim) / c;
+                int64_t lo = 0, hi = N; // first j with nu[j] - nuh > -del
+                while (lo < hi) {
+                    int64_t m = (lo + hi) >> 1;
+                    if (nu[m] - nuh > -del) hi = m; else lo = m + 1;
+                }
+                const int64_t jl = lo;
+                lo = 0;
+                hi = N; // first j with nu[j] - nuh >= del
+                while (lo < hi) {
+                    int64_t m = (lo + hi) >> 1;
+                    if (nu[m] - nuh >= del) hi = m; else lo = m + 1;
+                }
+                const int2 cut = jrange[l];
+                r.x = (int)max((int64_t)cut.x, jl);
+                r.y = (int)min((int64_t)cut.y, lo - 1);
+            }
+            jnear[idx] = r;
+        }
         cmin = (float)cr * (1.0f - 1e-6f);
         amin = (float)a * (1.0f - 1e-6f);
     }
@@ -209,23 +243,12 @@ template <> struct Off<float> {
         *hi = (float)o;
         *lo = (float)(o - (double)*hi);
     }
-    // (ohi - bhi) is exact when the point is near the line (Sterbenz); the lo parts ride along
-    __device__ static void dnu2(float ohi, float olo, float bhi, float blo, float* dh, float* dl)
-    {
-        *dh = ohi - bhi;
-        *dl = olo - blo;
-    }
 };
 template <> struct Off<double> {
     __device__ static void make(double v, double, double* hi, float* lo)
     {
         *hi = v;
         *lo = 0.0f;
-    }
-    __device__ static void dnu2(double ohi, float, double bhi, float, double* dh, double* dl)
-    {
-        *dh = ohi - bhi;
-        *dl = 0.0;
     }
 };
 
@@ -269,7 +292,7 @@ __device__ __forceinline__ void strip_window(const int2* jrange, int64_t nl, int
 }
 
 // Grid points of one warp: G per lane, lane-interleaved, offsets to the warp's
-// middle point.  Returns false when the warp has no point in the grid.
+// middle point.  init() returns false when the warp has no point in the grid.
 template <class R>
 struct WarpPoints {
     R ohi[LS_G];
@@ -278,7 +301,7 @@ struct WarpPoints {
     R ow0, ow1;   // their offsets
     double ref;
 
-    __device__ bool init(const double* nu, int64_t jbase, int64_t jlast, float* olo_s)
+    __device__ bool init(const double* nu, int64_t jbase, int64_t jlast)
     {
         const int lane = threadIdx.x & 31;
         if (jbase > jlast) return false;
@@ -289,7 +312,6 @@ struct WarpPoints {
             jg[g] = (int)j;
             float lo;
             Off<R>::make(nu[min64(j, jlast)], ref, &ohi[g], &lo);
-            olo_s[g * 32 + lane] = lo;
         }
         jw0 = (int)jbase;
         jw1 = (int)min64(jlast, jbase + 32 * LS_G - 1);
@@ -304,50 +326,54 @@ struct WarpPoints {
     }
 };
 
-// Lower bound of |z| over the warp's points for lines [bf, bl] (offsets, sorted):
-// true when every point is at |z|^2 >= z2 from every line.
-__device__ __forceinline__ bool all_far(float bf, float bl, float ow0, float ow1, float cmin, float amin, float z2)
+__device__ __forceinline__ bool in_range(int j, int2 r) { return j >= r.x && j <= r.y; }
+
+// A point takes a line's far form when it is inside the line's cut and outside
+// its near range.
+__device__ __forceinline__ bool far_point(int j, int2 cut, int2 nr) { return in_range(j, cut) && !in_range(j, nr); }
+
+// Does the line cover every point of [jw0, jw1] with its far form?
+__device__ __forceinline__ bool covers_far(int2 cut, int2 nr, int jw0, int jw1)
 {
-    float dist = fmaxf(fmaxf(bf - ow1, ow0 - bl), 0.0f);
-    float xm = dist * cmin;
-    return fmaf(xm, xm, amin * amin) >= z2;
+    const bool full = cut.x <= jw0 && cut.y >= jw1;
+    const bool clear = nr.x > nr.y || nr.y < jw0 || nr.x > jw1;
+    return full && clear;
 }
 
+// Forward tile: the fast-form constants, each duplicated so one broadcast load
+// fills a register pair for the packed two-point FP32 instructions (FP32 path),
+// plus what the FP64 path needs.
 template <class R>
 struct LineTile {
-    R bhi[32];
-    float blo[32];
-    R G[32], k0[32], f2[32];
-    typename vec4<R>::type k[32]; // k1..k4 of the fast form
-    typename vec4<R>::type r2[32];
-    R clo[32];
-    int2 jr[32];
-    // the fast-form constants again, each duplicated so that one broadcast load
-    // fills a register pair for the packed two-point FP32 instructions:
     float4 q0[32]; // (-b, -b, G, G)
     float4 q1[32]; // (k0, k0, k1, k1)
     float4 q2[32]; // (k2, k2, k3, k3)
     float4 q3[32]; // (k4, k4, F2, F2)
+    int2 jr[32], jn[32];
+    R bhi[32];
+    typename vec4<R>::type r2[32];
 };
 
-// Packed fast forms: two grid points per FP32 instruction (FADD2/FFMA2), one
-// reciprocal each.  Only the FP32 path has them; the FP64 path never takes a
-// fast branch.
-template <class R>
-__device__ __forceinline__ void fast_k1(const LineTile<R>&, const R (&)[LS_G], R (&)[LS_G])
+// Fast form of a line's term from the asymptotic series with K = 2 (Eq. asywofz),
+// written in rho = 1/(dnu^2 + gamma^2):  Av H = rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
+// with k0 = s gamma/pi = Al, B = 2 beta^2, G = gamma^2 and
+//   k1 = 1.5 B Al,  k2 = Al (3.75 B^2 - 2 G B),  k3 = -15 G B^2 Al,  k4 = 12 G^2 B^2 Al;
+// the K = 1 form keeps rho (k0 + rho (k1 + rho F2)), F2 = -2 G B Al.
+// From rec1 = {G, Al, F1 = 1.5 B Al, F2 = -2 G B Al} and c = 1/sqrt(B):
+__device__ __forceinline__ void fast_consts(const float4& p1, float c, float4* k)
 {
-}
-template <class R>
-__device__ __forceinline__ void fast_k2(const LineTile<R>&, const R (&)[LS_G], R (&)[LS_G])
-{
+    const float B = rcp_fast(c * c);
+    k->x = p1.z;                        // k1
+    k->y = fmaf(2.5f * B, p1.z, p1.w);  // k2
+    k->z = 7.5f * B * p1.w;             // k3
+    k->w = -6.0f * p1.x * B * p1.w;     // k4
 }
 
 __device__ __forceinline__ float2 f2lo(const float4& v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 f2hi(const float4& v) { return make_float2(v.z, v.w); }
 __device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(rcp_fast(v.x), rcp_fast(v.y)); }
 // both reciprocals from one: 1/D1 = D2/(D1 D2), 1/D2 = D1/(D1 D2) (about 1.5 ulp);
-// trades a second MUFU op for two FP32 multiplies.  D1 D2 stays in range in the fast
-// forms (0.01 < D < 1e4 there).
+// trades a second MUFU op for two FP32 multiplies (0.01 < D < 1e4 in the far forms)
 __device__ __forceinline__ float2 rcp2_shared(float2 v)
 {
     float r = rcp_fast(v.x * v.y);
@@ -357,213 +383,75 @@ __device__ __forceinline__ float2 rcp2_shared(float2 v)
 // the MUFU pipe (16 ops/clk/SM) against the FP32 pipe (128 lanes/clk/SM)
 __device__ __forceinline__ float2 rcp2_mix(float2 v, int p) { return (p < 2) ? rcp2_shared(v) : rcp2(v); }
 
-// K = 1: acc += rho (k0 + rho (k1 + rho F2)),  rho = 1/((o - b)^2 + G)
-template <>
-__device__ __forceinline__ void fast_k1<float>(const LineTile<float>& tl, const float (&ohi)[LS_G],
-                                               float (&acc)[LS_G])
-{
-    float2 o2[LS_G / 2], a2[LS_G / 2];
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
-        a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
-    }
-#pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
-        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v3 = tl.q3[i];
-        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), f2 = f2hi(v3);
-#pragma unroll
-        for (int p = 0; p < LS_G / 2; ++p) {
-            float2 d = __fadd2_rn(o2[p], nb);
-            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
-            float2 u = __ffma2_rn(__ffma2_rn(f2, rho, k1), rho, k0);
-            a2[p] = __ffma2_rn(rho, u, a2[p]);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        acc[2 * p] = a2[p].x;
-        acc[2 * p + 1] = a2[p].y;
-    }
-}
-
-// K = 2: acc += rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
-template <>
-__device__ __forceinline__ void fast_k2<float>(const LineTile<float>& tl, const float (&ohi)[LS_G],
-                                               float (&acc)[LS_G])
-{
-    float2 o2[LS_G / 2], a2[LS_G / 2];
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
-        a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
-    }
-#pragma unroll 2
-    for (int i = 0; i < 32; ++i) {
-        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v2 = tl.q2[i], v3 = tl.q3[i];
-        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), k2 = f2lo(v2), k3 = f2hi(v2),
-                     k4 = f2lo(v3);
-#pragma unroll
-        for (int p = 0; p < LS_G / 2; ++p) {
-            float2 d = __fadd2_rn(o2[p], nb);
-            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
-            float2 u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(k4, rho, k3), rho, k2), rho, k1), rho, k0);
-            a2[p] = __ffma2_rn(rho, u, a2[p]);
-        }
-    }
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        acc[2 * p] = a2[p].x;
-        acc[2 * p + 1] = a2[p].y;
-    }
-}
-
-// Fast form of a line's term from the asymptotic series with K = 2 (Eq. asywofz),
-// written in rho = 1/(dnu^2 + gamma^2):  Av H = rho (k0 + rho (k1 + rho (k2 + rho (k3 + rho k4))))
-// with k0 = s gamma/pi = Al, B = 2 beta^2, G = gamma^2 and
-//   k1 = 1.5 B Al,  k2 = Al (3.75 B^2 - 2 G B),  k3 = -15 G B^2 Al,  k4 = 12 G^2 B^2 Al.
-// From rec1 = {G, Al, F1 = 1.5 B Al, F2 = -2 G B Al} and c = 1/sqrt(B):
-template <class R>
-__device__ __forceinline__ void fast_coeffs(const typename vec4<R>::type& p1, R c, R* k0,
-                                            typename vec4<R>::type* k)
-{
-    R B = rcp_fast(c * c);
-    *k0 = p1.y;
-    k->x = p1.z;
-    k->y = fma(R(2.5) * B, p1.z, p1.w);
-    k->z = R(7.5) * B * p1.w;
-    k->w = R(-6) * p1.x * B * p1.w;
-}
-
-// one lane's line record as loaded from global memory
-// ---- mixed chunks (FP32 only): per-line dispatch with packed arithmetic
-
-// K = 2 form over lines [i0, i1) of the tile; when masked, each point only takes
-// the lines whose cut range holds it.
-__device__ __forceinline__ void k2_lines(const LineTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
-                                         float2 (&a2)[LS_G / 2], bool masked, const int (&jg)[LS_G])
-{
-    for (int i = i0; i < i1; ++i) {
-        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v2 = tl.q2[i], v3 = tl.q3[i];
-        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1), k2 = f2lo(v2), k3 = f2hi(v2),
-                     k4 = f2lo(v3);
-        const int2 jr = tl.jr[i];
-#pragma unroll
-        for (int p = 0; p < LS_G / 2; ++p) {
-            float2 d = __fadd2_rn(o2[p], nb);
-            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
-            float2 u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(k4, rho, k3), rho, k2), rho, k1), rho, k0);
-            if (masked) {
-                rho.x = (jg[2 * p] >= jr.x && jg[2 * p] <= jr.y) ? rho.x : 0.0f;
-                rho.y = (jg[2 * p + 1] >= jr.x && jg[2 * p + 1] <= jr.y) ? rho.y : 0.0f;
-            }
-            a2[p] = __ffma2_rn(rho, u, a2[p]);
-        }
-    }
-}
-
-// One line near the warp's points: the K = 5 form in rho (coefficients ctab[0..10],
-// see k5_coeff) at every point with |z| >= 8, i.e. dnu^2 >= dthr2, and the small-|z|
-// series (dtab, see w_series_rec) at the others.
-__device__ __forceinline__ void near_line(const LineTile<float>& tl, int i, const float (&ohi)[LS_G],
-                                          const float* olo, const float* ctab, const float* dtab,
+// Packed forms over lines [i0, i1) of a tile.  KIND 1: K = 1, unmasked; KIND 2:
+// K = 2, unmasked; KIND 3: K = 2, masked per (line, point) by far_point.
+template <int KIND>
+__device__ __forceinline__ void far_lines(const LineTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                           float2 (&a2)[LS_G / 2], const int (&jg)[LS_G])
 {
-    const int lane = threadIdx.x & 31;
-    const float bh = tl.bhi[i], bl = tl.blo[i], G = tl.G[i], cl = tl.clo[i];
-    const float4 p2 = tl.r2[i];
-    const int2 jr = tl.jr[i];
-    const float a = p2.y, c = p2.x;
-    const float dthr2 = fmaxf(Tier<float>::z2_series - a * a, 0.0f) * rcp_fast(c * c);
-    float dh[LS_G], dl[LS_G];
-    float2 rho[LS_G / 2], u[LS_G / 2];
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int g = 2 * p + q;
-            dh[g] = ohi[g] - bh;
-            dl[g] = olo[g * 32 + lane] - bl;
+#pragma unroll 2
+    for (int i = i0; i < i1; ++i) {
+        const float4 v0 = tl.q0[i], v1 = tl.q1[i], v3 = tl.q3[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1);
+        float4 v2 = make_float4(0.f, 0.f, 0.f, 0.f);
+        int2 cut = make_int2(0, 0), nr = make_int2(1, 0);
+        if (KIND != 1) v2 = tl.q2[i];
+        if (KIND == 3) {
+            cut = tl.jr[i];
+            nr = tl.jn[i];
         }
-        float2 d = __fadd2_rn(make_float2(dh[2 * p], dh[2 * p + 1]), make_float2(dl[2 * p], dl[2 * p + 1]));
-        rho[p] = rcp2(__ffma2_rn(d, d, make_float2(G, G)));
-        const float cc = ctab[10];
-        u[p] = make_float2(cc, cc);
-    }
 #pragma unroll
-    for (int n = 9; n >= 0; --n) {
-        const float cc = ctab[n];
-        const float2 c2 = make_float2(cc, cc);
-#pragma unroll
-        for (int p = 0; p < LS_G / 2; ++p) u[p] = __ffma2_rn(u[p], rho[p], c2);
-    }
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        float2 v = __fmul2_rn(rho[p], u[p]);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int g = 2 * p + q;
-            const float d = dh[g] + dl[g];
-            const bool in = jg[g] >= jr.x && jg[g] <= jr.y;
-            float add = (q == 0) ? v.x : v.y;
-            if (!(in && d * d >= dthr2)) add = 0.0f;
-            if (__any_sync(0xffffffffu, in && d * d < dthr2)) {
-                if (in && d * d < dthr2) {
-                    float x, xl;
-                    scaled_pair(dh[g], dl[g], c, cl, &x, &xl);
-                    add = p2.z * voigt_H_series(x, xl, a, p2.w, dtab);
-                }
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
+            float2 u;
+            if (KIND == 1)
+                u = __ffma2_rn(__ffma2_rn(f2hi(v3), rho, k1), rho, k0);
+            else
+                u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(f2lo(v3), rho, f2hi(v2)), rho, f2lo(v2)), rho, k1),
+                               rho, k0);
+            if (KIND == 3) {
+                rho.x = far_point(jg[2 * p], cut, nr) ? rho.x : 0.0f;
+                rho.y = far_point(jg[2 * p + 1], cut, nr) ? rho.y : 0.0f;
             }
-            if (q == 0) a2[p].x += add; else a2[p].y += add;
+            a2[p] = __ffma2_rn(rho, u, a2[p]);
         }
     }
 }
 
-// Whole mixed chunk: runs of lines that are far (|z| >= 25 at every point) and
-// cover the warp go through the packed K = 2 loop; far lines that cover only part
-// of the warp take it masked; the rest go through near_line.
-__device__ __forceinline__ void mixed_chunk(const LineTile<float>& tl, const WarpPoints<float>& pts,
-                                            const float* olo, float* ctab, float* dtab, float (&acc)[LS_G])
+// One 32-line chunk of the FP32 main kernel.
+__device__ __forceinline__ void chunk_far(const LineTile<float>& tl, const WarpPoints<float>& pts, float cmin,
+                                          float amin, float (&acc)[LS_G])
 {
     const int lane = threadIdx.x & 31;
-    // classify line `lane`
-    const float bh = tl.bhi[lane];
-    const float4 p2 = tl.r2[lane];
-    const int2 jr = tl.jr[lane];
-    const float dist = fmaxf(fmaxf(bh - pts.ow1, pts.ow0 - bh), 0.0f);
-    const float xm = dist * p2.x;
-    const bool far = fmaf(xm, xm, p2.y * p2.y) >= Tier<float>::z2_fast;
-    const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
-    const unsigned fm = __ballot_sync(0xffffffffu, far && full);
-    const unsigned em = __ballot_sync(0xffffffffu, far && !full);
-
+    const unsigned ok = __ballot_sync(0xffffffffu, covers_far(tl.jr[lane], tl.jn[lane], pts.jw0, pts.jw1));
     float2 o2[LS_G / 2], a2[LS_G / 2];
 #pragma unroll
     for (int p = 0; p < LS_G / 2; ++p) {
         o2[p] = make_float2(pts.ohi[2 * p], pts.ohi[2 * p + 1]);
         a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
     }
-    int i = 0;
-    while (i < 32) {
-        const unsigned rest = fm >> i;
-        if (rest & 1u) {
-            const unsigned zeros = ~rest;
-            const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
-            k2_lines(tl, i, j, o2, a2, false, pts.jg);
-            i = j;
-        } else if ((em >> i) & 1u) {
-            k2_lines(tl, i, i + 1, o2, a2, true, pts.jg);
-            ++i;
-        } else {
-            // per-line tables shared by the warp
-            const float4 q = tl.r2[i];
-            const float hn = (float)(lane + 1) * Tier<float>::h;
-            __syncwarp();
-            dtab[lane] = rcp_fast(fmaf(hn, hn, q.y * q.y));
-            if (lane < 11) ctab[lane] = k5_coeff(lane, tl.k0[i], rcp_fast(q.x * q.x), tl.G[i]);
-            __syncwarp();
-            near_line(tl, i, pts.ohi, olo, ctab, dtab, a2, pts.jg);
-            ++i;
+    if (ok == 0xffffffffu) {
+        // every pair at |z| >= 25; K = 1 suffices when every pair is at |z| >= 100
+        const float dist = fmaxf(fmaxf(-tl.q0[0].x - pts.ow1, pts.ow0 + tl.q0[31].x), 0.0f);
+        const float xm = dist * cmin;
+        if (fmaf(xm, xm, amin * amin) >= 1.0e4f)
+            far_lines<1>(tl, 0, 32, o2, a2, pts.jg);
+        else
+            far_lines<2>(tl, 0, 32, o2, a2, pts.jg);
+    } else {
+        int i = 0;
+        while (i < 32) {
+            const unsigned rest = ok >> i;
+            if (rest & 1u) {
+                const unsigned zeros = ~rest;
+                const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
+                far_lines<2>(tl, i, j, o2, a2, pts.jg);
+                i = j;
+            } else {
+                far_lines<3>(tl, i, i + 1, o2, a2, pts.jg);
+                ++i;
+            }
         }
     }
 #pragma unroll
@@ -573,43 +461,48 @@ __device__ __forceinline__ void mixed_chunk(const LineTile<float>& tl, const War
     }
 }
 
-template <class R>
-__device__ __forceinline__ void mixed_chunk_dispatch(const LineTile<R>&, const WarpPoints<R>&, const float*, float*,
-                                                     float*, R (&)[LS_G])
+// One 32-line chunk of the FP64 main kernel: every in-cut pair, tiered Faddeeva.
+__device__ __forceinline__ void chunk_fp64(const LineTile<double>& tl, const WarpPoints<double>& pts,
+                                           double (&acc)[LS_G])
 {
-}
-template <>
-__device__ __forceinline__ void mixed_chunk_dispatch<float>(const LineTile<float>& tl, const WarpPoints<float>& pts,
-                                                            const float* olo, float* ctab, float* dtab,
-                                                            float (&acc)[LS_G])
-{
-    mixed_chunk(tl, pts, olo, ctab, dtab, acc);
+    for (int i = 0; i < 32; ++i) {
+        const double bh = tl.bhi[i];
+        const double4_32a p2 = tl.r2[i];
+        const int2 jr = tl.jr[i];
+#pragma unroll
+        for (int g = 0; g < LS_G; ++g) {
+            if (in_range(pts.jg[g], jr)) {
+                const double x = fabs(pts.ohi[g] - bh) * p2.x;
+                acc[g] = fma(p2.z, voigt_H<double>(x, 0.0, p2.y, p2.w, nullptr), acc[g]);
+            }
+        }
+    }
 }
 
+// one lane's line record as loaded from global memory
 template <class R>
 struct LineRec {
     double nu;
     typename vec4<R>::type p1, p2;
-    R cl;
-    int2 jr;
+    int2 jr, jn;
 
     __device__ void load(const double* nu_hat, const int2* jrange, const typename vec4<R>::type* rec1,
-                         const typename vec4<R>::type* rec2, const R* clo, int64_t l, int64_t ce)
+                         const typename vec4<R>::type* rec2, const int2* jnear, int64_t l, int64_t ce)
     {
         if (l < ce) {
             nu = nu_hat[l];
             p1 = rec1[l];
             p2 = rec2[l];
-            cl = clo[l];
             jr = jrange[l];
+            jn = jnear ? jnear[l] : make_int2(1, 0);
         } else {
             // padding: the chunk's last line with zero amplitude keeps every
-            // sub-tile test and offset that of real lines
+            // chunk test and offset that of real lines
             nu = nu_hat[ce - 1];
             jr = jrange[ce - 1];
+            jn = jnear ? jnear[ce - 1] : make_int2(1, 0);
             p1.x = R(1); p1.y = R(0); p1.z = R(0); p1.w = R(0);
             p2.x = R(1); p2.y = R(1); p2.z = R(0); p2.w = R(0);
-            cl = R(0);
         }
     }
 };
@@ -618,26 +511,20 @@ template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
-    const R* __restrict__ clo, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N, int64_t nl,
-    int layer0, int ksplit, double unscale, void* __restrict__ sigma, int sigma_is_float, double* __restrict__ partial,
-    int L_total)
+    const int2* __restrict__ jnear, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N,
+    int64_t nl, int layer0, int ksplit, double unscale, void* __restrict__ sigma, int sigma_is_float,
+    double* __restrict__ partial, int L_total, const double* __restrict__ near_sum)
 {
     using R4 = typename vec4<R>::type;
     __shared__ LineTile<R> tiles[LS_WARPS];
-    __shared__ float olo_s[LS_WARPS][32 * LS_G];
-    __shared__ R dtab_s[LS_WARPS][32];
-    __shared__ float ctab_s[LS_WARPS][12];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
     const int64_t j0 = (int64_t)strip * LS_STRIP;
     const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
     LineTile<R>& tl = tiles[w];
-    float* olo = olo_s[w];
-    R* dtab = dtab_s[w];
-    float* ctab = ctab_s[w];
 
     WarpPoints<R> pts;
-    if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast, olo)) return;
+    if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) return;
     int64_t cb, ce;
     strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
     const int layer = layer0 + nloc;
@@ -645,7 +532,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
     const R4* r1g = rec1 + lay;
     const R4* r2g = rec2 + lay;
-    const R* clg = clo + lay;
+    const int2* jng = FAST ? jnear + lay : nullptr;
 
     R acc[LS_G], shi[LS_G], slo[LS_G];
 #pragma unroll
@@ -655,7 +542,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
         slo[g] = R(0);
     }
     LineRec<R> nx;
-    if (cb < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, cb + lane, ce);
+    if (cb < ce) nx.load(nu_hat, jrange, r1g, r2g, jng, cb + lane, ce);
 
     for (int64_t t0 = cb; t0 < ce; t0 += 32) {
         {
@@ -663,111 +550,28 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
             float bl;
             Off<R>::make(nx.nu, pts.ref, &bh, &bl);
             tl.bhi[lane] = bh;
-            tl.blo[lane] = bl;
-            R k0;
-            R4 kk;
-            fast_coeffs<R>(nx.p1, nx.p2.x, &k0, &kk);
-            tl.G[lane] = nx.p1.x;
-            tl.k0[lane] = k0;
-            tl.f2[lane] = nx.p1.w;
-            tl.k[lane] = kk;
             tl.r2[lane] = nx.p2;
-            tl.clo[lane] = nx.cl;
             tl.jr[lane] = nx.jr;
+            tl.jn[lane] = nx.jn;
             if (FAST) {
-                const float nbf = -(float)bh, Gf = (float)nx.p1.x;
-                tl.q0[lane] = make_float4(nbf, nbf, Gf, Gf);
-                tl.q1[lane] = make_float4((float)k0, (float)k0, (float)kk.x, (float)kk.x);
-                tl.q2[lane] = make_float4((float)kk.y, (float)kk.y, (float)kk.z, (float)kk.z);
-                tl.q3[lane] = make_float4((float)kk.w, (float)kk.w, (float)nx.p1.w, (float)nx.p1.w);
+                float4 k;
+                fast_consts(make_float4((float)nx.p1.x, (float)nx.p1.y, (float)nx.p1.z, (float)nx.p1.w),
+                            (float)nx.p2.x, &k);
+                const float nb = -(float)bh, G = (float)nx.p1.x, k0 = (float)nx.p1.y;
+                tl.q0[lane] = make_float4(nb, nb, G, G);
+                tl.q1[lane] = make_float4(k0, k0, k.x, k.x);
+                tl.q2[lane] = make_float4(k.y, k.y, k.z, k.z);
+                tl.q3[lane] = make_float4(k.w, k.w, (float)nx.p1.w, (float)nx.p1.w);
             }
         }
         __syncwarp();
-        if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, clg, t0 + 32 + lane, ce); // in flight meanwhile
+        if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, jng, t0 + 32 + lane, ce); // in flight meanwhile
 
-        // chunk class: 2 = every (line, point) at |z| >= 100 (K = 1 form),
-        // 1 = at |z| >= 25 (K = 2 form), 0 = mixed (per line, per point)
-        int cls = 0;
-        if (FAST) {
-            bool incut = (tl.jr[31].x <= pts.jw0) && (tl.jr[0].y >= pts.jw1);
-            if (incut) {
-                float dist = fmaxf(fmaxf((float)tl.bhi[0] - (float)pts.ow1, (float)pts.ow0 - (float)tl.bhi[31]), 0.0f);
-                float xm = dist * cmin;
-                float z2 = fmaf(xm, xm, amin * amin);
-                cls = (z2 >= (float)Tier<R>::z2_far) ? 2 : (z2 >= (float)Tier<R>::z2_fast) ? 1 : 0;
-            }
-        }
-        if (cls == 2) {
-            // K = 1: Av H = rho (k0 + rho (k1 + rho F2)), F2 = -2 G B Al, rho = 1/(dnu^2 + gamma^2);
-            // the K = 2 terms are below 4e-8 of a line's value here
-            fast_k1<R>(tl, pts.ohi, acc);
-        } else if (cls == 1) {
-            fast_k2<R>(tl, pts.ohi, acc);
-        } else if (FAST) {
-            mixed_chunk_dispatch<R>(tl, pts, olo, ctab, (float*)dtab, acc);
-        } else {
-            // FP64: per line (warp-uniform): if every point of the warp is at |z| >= 100
-            // use the Lorentz-wing form, masked by the cut only when the line does
-            // not cover the whole warp; else choose the Faddeeva tier per point.
-            for (int i = 0; i < 32; ++i) {
-                const R bh = tl.bhi[i];
-                const R4 p2 = tl.r2[i];
-                const int2 jr = tl.jr[i];
-                const R G = tl.G[i], k0 = tl.k0[i];
-                const R4 k = tl.k[i];
-                bool line_far = false;
-                if (FAST)
-                    line_far = all_far((float)bh, (float)bh, (float)pts.ow0, (float)pts.ow1, (float)p2.x, (float)p2.y,
-                                       (float)Tier<R>::z2_fast);
-                if (line_far) {
-                    const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
-#pragma unroll
-                    for (int g = 0; g < LS_G; ++g) {
-                        R d = pts.ohi[g] - bh;
-                        R rho = rcp_fast(fma(d, d, G));
-                        R u = fma(fma(fma(fma(k.w, rho, k.z), rho, k.y), rho, k.x), rho, k0);
-                        R v = rho * u;
-                        if (full || (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y)) acc[g] += v;
-                    }
-                } else {
-                    const float bl = tl.blo[i];
-                    const R cl = tl.clo[i];
-                    if (FAST) {
-                        // per line, shared by the warp: 1/(n^2 h^2 + a^2) (n = 1..32) for the
-                        // small-|z| series, and the 11 coefficients of the K = 5 form in rho
-                        const R hn = R(lane + 1) * (R)Tier<R>::h;
-                        __syncwarp();
-                        dtab[lane] = rcp_fast(fma(hn, hn, p2.y * p2.y));
-                        if (lane < 11) ctab[lane] = k5_coeff(lane, (float)k0, (float)rcp_fast(p2.x * p2.x), (float)G);
-                        __syncwarp();
-                    }
-#pragma unroll
-                    for (int g = 0; g < LS_G; ++g) {
-                        if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
-                            R dh, dl, x, xl;
-                            Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
-                            scaled_pair(dh, dl, p2.x, cl, &x, &xl);
-                            const R z2 = fma(x, x, p2.y * p2.y);
-                            if (FAST && z2 >= (R)Tier<R>::z2_series) {
-                                // |z| >= 8: K = 5 asymptotic form, uniform across the warp
-                                R d = dh + dl;
-                                R rho = rcp_fast(fma(d, d, G));
-                                R u = (R)ctab[10];
-#pragma unroll
-                                for (int n = 9; n >= 0; --n) u = fma(u, rho, (R)ctab[n]);
-                                acc[g] = fma(rho, u, acc[g]);
-                            } else if (FAST) {
-                                acc[g] = fma(p2.z, (R)voigt_H_series((float)x, (float)xl, (float)p2.y, (float)p2.w,
-                                                                     (const float*)dtab),
-                                             acc[g]);
-                            } else {
-                                acc[g] = fma(p2.z, voigt_H<R>(x, xl, p2.y, p2.w, nullptr), acc[g]);
-                            }
-                        }
-                    }
-                }
-            }
-        }
+        if constexpr (FAST)
+            chunk_far(tl, pts, cmin, amin, acc);
+        else
+            chunk_fp64(tl, pts, acc);
+
         // fold the 32-line partial into the running compensated sum (TwoSum)
 #pragma unroll
         for (int g = 0; g < LS_G; ++g) {
@@ -784,6 +588,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     for (int g = 0; g < LS_G; ++g) {
         if (pts.jg[g] <= jlast) {
             double v = (double)shi[g] + (double)slo[g];
+            if (FAST && kc == 0) v += near_sum[(size_t)nloc * N + pts.jg[g]];
             size_t o = (size_t)layer * N + pts.jg[g];
             if (ksplit == 1) {
                 if (sigma_is_float)
@@ -814,57 +619,200 @@ __global__ void combine_kernel(const double* __restrict__ partial, int ksplit, i
     if (sigma_is_float) ((float*)sigma)[o] = (float)s; else ((double*)sigma)[o] = s;
 }
 
-// ------------------------------------------------------------------ K6: adjoint
+// ------------------------------------------------------------------ near kernels (FP32 path)
 
-template <class R>
-struct AdjTile {
-    R bhi[32];
-    float blo[32];
-    typename vec4<R>::type r2[32];
-    typename vec4<R>::type t[32]; // fast form: f_T = rho (T1 + rho (T2 + rho (T3 + rho T4)))
-    typename vec4<R>::type u[32]; // fast form: f_b = rho (U1 + rho (U2 + rho (U3 + rho U4)))
-    R G[32], clo[32], aS[32], nn[32];
-    int2 jr[32];
-    // duplicated constants for the packed fast form (FP32 path only)
-    float4 q0[32];           // (-b, -b, G, G)
-    float4 qt0[32], qt1[32]; // (T1, T1, T2, T2), (T3, T3, T4, T4)
-    float4 qu0[32], qu1[32]; // (U1, U1, U2, U2), (U3, U3, U4, U4)
+constexpr int NR_THREADS = 128;
+
+// Lines staged by a near-kernel warp: offsets to the warp's reference point
+// (hi + lo), near ranges and per-line scalars.
+struct NearTile {
+    float bhi[32], blo[32], clo[32];
+    float4 r2[32]; // c, a, Av, Kc
+    int2 jn[32];
+    float aS[32], nn[32];
 };
 
-template <class R>
-__device__ __forceinline__ void fast_adj(const AdjTile<R>&, const R (&)[LS_G], const R (&)[LS_G], R&, R&)
+// Candidate lines of a warp's 32 points: centres within sqrt(625 - a^2)/c < 25/cmin
+// of any of them (binary search on the sorted centres), cut to chunks of 32.
+__device__ __forceinline__ void near_window(const double* nu_hat, int64_t nl, double lo_nu, double hi_nu, double del,
+                                            int64_t* b, int64_t* e)
 {
-}
-// lambda rho P_T(rho) and lambda rho P_U(rho), two points per packed instruction
-template <>
-__device__ __forceinline__ void fast_adj<float>(const AdjTile<float>& tl, const float (&ohi)[LS_G],
-                                                const float (&lam)[LS_G], float& accT, float& accB)
-{
-    float2 o2[LS_G / 2], l2[LS_G / 2];
-#pragma unroll
-    for (int p = 0; p < LS_G / 2; ++p) {
-        o2[p] = make_float2(ohi[2 * p], ohi[2 * p + 1]);
-        l2[p] = make_float2(lam[2 * p], lam[2 * p + 1]);
+    long long bb = 0, ee = 0;
+    if ((threadIdx.x & 31) == 0) {
+        int64_t lo = 0, hi = nl;
+        while (lo < hi) {
+            int64_t m = (lo + hi) >> 1;
+            if (nu_hat[m] < lo_nu - del) lo = m + 1; else hi = m;
+        }
+        bb = lo;
+        lo = bb;
+        hi = nl;
+        while (lo < hi) {
+            int64_t m = (lo + hi) >> 1;
+            if (nu_hat[m] <= hi_nu + del) lo = m + 1; else hi = m;
+        }
+        ee = lo;
     }
-    float2 aT = make_float2(accT, 0.0f), aB = make_float2(accB, 0.0f);
-#pragma unroll 2
-    for (int i = 0; i < 32; ++i) {
-        const float4 v0 = tl.q0[i], t0 = tl.qt0[i], t1 = tl.qt1[i], u0 = tl.qu0[i], u1 = tl.qu1[i];
-        const float2 nb = f2lo(v0), G = f2hi(v0);
-#pragma unroll
-        for (int p = 0; p < LS_G / 2; ++p) {
-            float2 d = __fadd2_rn(o2[p], nb);
-            float2 rho = rcp2(__ffma2_rn(d, d, G));
-            float2 lr = __fmul2_rn(l2[p], rho);
-            float2 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
-            float2 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
-            aT = __ffma2_rn(lr, pt, aT);
-            aB = __ffma2_rn(lr, pu, aB);
+    *b = __shfl_sync(0xffffffffu, bb, 0);
+    *e = __shfl_sync(0xffffffffu, ee, 0);
+}
+
+// near_sum[n][j] = sum over lines with j in their near range of Av H(x, a),
+// one thread per grid point, lines in ascending order, Neumaier-compensated.
+__global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __restrict__ nu_hat, int64_t nl,
+                                                              const float4* __restrict__ rec2,
+                                                              const float* __restrict__ clo,
+                                                              const int2* __restrict__ jnear,
+                                                              const float* __restrict__ agg,
+                                                              const double* __restrict__ nu, int64_t N, int layer0,
+                                                              double* __restrict__ near_sum)
+{
+    __shared__ NearTile tiles[NR_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nloc = blockIdx.y;
+    const int64_t jb = (int64_t)blockIdx.x * NR_THREADS + w * 32;
+    if (jb >= N) return;
+    const int64_t jl = min64(N - 1, jb + 31);
+    const int64_t j = jb + lane;
+    const int64_t jc = min64(j, N - 1);
+    const double ref = nu[jb];
+    const double oj = nu[jc] - ref;
+    const float ohi = (float)oj, olo = (float)(oj - (double)ohi);
+    const float cmin = agg[2 * (layer0 + nloc)];
+    const size_t lay = (size_t)nloc * nl;
+    NearTile& tl = tiles[w];
+    int64_t cb, ce;
+    near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
+    float sum = 0.0f, comp = 0.0f;
+    for (int64_t t0 = cb; t0 < ce; t0 += 32) {
+        const int64_t l = t0 + lane;
+        __syncwarp();
+        if (l < ce) {
+            const double o = nu_hat[l] - ref;
+            const float bh = (float)o;
+            tl.bhi[lane] = bh;
+            tl.blo[lane] = (float)(o - (double)bh);
+            tl.r2[lane] = rec2[lay + l];
+            tl.clo[lane] = clo[lay + l];
+            tl.jn[lane] = jnear[lay + l];
+        } else {
+            tl.jn[lane] = make_int2(1, 0);
+        }
+        __syncwarp();
+        const int nt = (int)min64(32, ce - t0);
+        for (int i = 0; i < nt; ++i) {
+            const int2 nr = tl.jn[i];
+            if (j <= jl && in_range((int)j, nr)) {
+                const float4 p2 = tl.r2[i];
+                float x, xl;
+                scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
+                float wr, wi;
+                faddeeva<float>(x, xl, p2.y, p2.w, &wr, &wi);
+                const float v = p2.z * wr;
+                const float t = sum + v;
+                comp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
+                sum = t;
+            }
         }
     }
-    accT = aT.x + aT.y;
-    accB = aB.x + aB.y;
+    if (j <= jl) near_sum[(size_t)nloc * N + j] = (double)sum + (double)comp;
 }
+
+// The adjoint's near pairs: per point, sum of lambda_j (f_T, f_b) (see
+// linesum_adjoint_kernel), reduced per block into part[layer][block].
+__global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
+    const double* __restrict__ nu_hat, int64_t nl, const float4* __restrict__ rec2, const float* __restrict__ clo,
+    const float* __restrict__ rec3, const int2* __restrict__ jnear, const float* __restrict__ agg,
+    const double* __restrict__ nu, int64_t N, int layer0, const double* __restrict__ T,
+    const double* __restrict__ g_sigma, double lam_scale, double* __restrict__ part)
+{
+    __shared__ NearTile tiles[NR_THREADS / 32];
+    __shared__ double red[2][NR_THREADS / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nloc = blockIdx.y;
+    const int layer = layer0 + nloc;
+    const int64_t jb = (int64_t)blockIdx.x * NR_THREADS + w * 32;
+    double sT = 0.0, sB = 0.0;
+    if (jb < N) {
+        const int64_t jl = min64(N - 1, jb + 31);
+        const int64_t j = jb + lane;
+        const int64_t jc = min64(j, N - 1);
+        const double ref = nu[jb];
+        const double oj = nu[jc] - ref;
+        const float ohi = (float)oj, olo = (float)(oj - (double)ohi);
+        const float cmin = agg[2 * layer];
+        const float half_invT = (float)(0.5 / T[layer]);
+        const float lam = (j <= jl) ? (float)(g_sigma[(size_t)layer * N + j] * lam_scale) : 0.0f;
+        const size_t lay = (size_t)nloc * nl;
+        NearTile& tl = tiles[w];
+        int64_t cb, ce;
+        near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
+        float aT = 0.0f, aB = 0.0f;
+        for (int64_t t0 = cb; t0 < ce; t0 += 32) {
+            const int64_t l = t0 + lane;
+            __syncwarp();
+            if (l < ce) {
+                const double o = nu_hat[l] - ref;
+                const float bh = (float)o;
+                tl.bhi[lane] = bh;
+                tl.blo[lane] = (float)(o - (double)bh);
+                tl.r2[lane] = rec2[lay + l];
+                tl.clo[lane] = clo[lay + l];
+                tl.jn[lane] = jnear[lay + l];
+                tl.aS[lane] = rec3[2 * (lay + l)];
+                tl.nn[lane] = rec3[2 * (lay + l) + 1];
+            } else {
+                tl.jn[lane] = make_int2(1, 0);
+            }
+            __syncwarp();
+            const int nt = (int)min64(32, ce - t0);
+            for (int i = 0; i < nt; ++i) {
+                const int2 nr = tl.jn[i];
+                if (j <= jl && in_range((int)j, nr)) {
+                    const float4 p2 = tl.r2[i];
+                    float x, xl;
+                    scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
+                    const float a = p2.y;
+                    float wr, wi, dr, di;
+                    faddeeva_d<float>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
+                    // H_x = Re w', H_a = -Im w'
+                    const float V0 = p2.z * wr;
+                    const float V1 = p2.z * x * dr;
+                    const float V2 = -p2.z * a * di;
+                    const float Db = -(V0 + V1 + V2);
+                    const float ft = tl.aS[i] * V0 + half_invT * Db + tl.nn[i] * V2;
+                    aT = fmaf(lam, ft, aT);
+                    aB = fmaf(lam, V2, aB);
+                }
+            }
+            sT += (double)aT;
+            sB += (double)aB;
+            aT = 0.0f;
+            aB = 0.0f;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        sT += __shfl_xor_sync(0xffffffffu, sT, o);
+        sB += __shfl_xor_sync(0xffffffffu, sB, o);
+    }
+    if (lane == 0) {
+        red[0][w] = sT;
+        red[1][w] = sB;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0.0, b = 0.0;
+        for (int i = 0; i < NR_THREADS / 32; ++i) {
+            a += red[0][i];
+            b += red[1][i];
+        }
+        const size_t o = (size_t)layer * gridDim.x + blockIdx.x;
+        part[2 * o] = a;
+        part[2 * o + 1] = b;
+    }
+}
+
+// ------------------------------------------------------------------ K6: adjoint
 
 // Per evaluation the adjoint accumulates
 //   f_T = (dlnS/dT) V0 + (1/(2T)) D_beta + (-n/T) D_gamma   and   f_b = D_gamma
@@ -873,19 +821,124 @@ __device__ __forceinline__ void fast_adj<float>(const AdjTile<float>& tl, const 
 // In the Lorentz-wing form (K = 1 of the asymptotic series, rho = 1/(dnu^2 + gamma^2),
 // B = 2 beta^2, G = gamma^2, Al = s gamma/pi):
 //   V0 = Al (rho + 1.5 B rho^2 - 2 G B rho^3),  D_beta = Al B (3 rho^2 - 4 G rho^3),
-//   D_gamma = Al (rho + (1.5 B - 2 G) rho^2 - 12 G B rho^3 + 12 G^2 B rho^4).
+//   D_gamma = Al (rho + (1.5 B - 2 G) rho^2 - 12 G B rho^3 + 12 G^2 B rho^4),
+// so f_T = rho (T1 + rho (T2 + rho (T3 + rho T4))) and f_b = rho (U1 + ... U4) with
+// per-line coefficients.  At |z| >= 25 the K = 2 terms are below 6e-6 of a term.
+template <class R>
+struct AdjTile {
+    float4 q0[32];           // (-b, -b, G, G)
+    float4 qt0[32], qt1[32]; // (T1, T1, T2, T2), (T3, T3, T4, T4)
+    float4 qu0[32], qu1[32]; // (U1, U1, U2, U2), (U3, U3, U4, U4)
+    int2 jr[32], jn[32];
+    R bhi[32];
+    typename vec4<R>::type r2[32];
+    R aS[32], nn[32];
+};
+
+// packed K = 1 adjoint over lines [i0, i1); MASKED: per (line, point) by far_point
+template <bool MASKED>
+__device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
+                                              const float2 (&l2)[LS_G / 2], float2& aT, float2& aB,
+                                              const int (&jg)[LS_G])
+{
+#pragma unroll 2
+    for (int i = i0; i < i1; ++i) {
+        const float4 v0 = tl.q0[i], t0 = tl.qt0[i], t1 = tl.qt1[i], u0 = tl.qu0[i], u1 = tl.qu1[i];
+        const float2 nb = f2lo(v0), G = f2hi(v0);
+        int2 cut = make_int2(0, 0), nr = make_int2(1, 0);
+        if (MASKED) {
+            cut = tl.jr[i];
+            nr = tl.jn[i];
+        }
+#pragma unroll
+        for (int p = 0; p < LS_G / 2; ++p) {
+            float2 d = __fadd2_rn(o2[p], nb);
+            float2 rho = rcp2(__ffma2_rn(d, d, G));
+            float2 lr = __fmul2_rn(l2[p], rho);
+            if (MASKED) {
+                lr.x = far_point(jg[2 * p], cut, nr) ? lr.x : 0.0f;
+                lr.y = far_point(jg[2 * p + 1], cut, nr) ? lr.y : 0.0f;
+            }
+            float2 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
+            float2 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
+            aT = __ffma2_rn(lr, pt, aT);
+            aB = __ffma2_rn(lr, pu, aB);
+        }
+    }
+}
+
+__device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const WarpPoints<float>& pts,
+                                              const float (&lam)[LS_G], float& accT, float& accB)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned ok = __ballot_sync(0xffffffffu, covers_far(tl.jr[lane], tl.jn[lane], pts.jw0, pts.jw1));
+    float2 o2[LS_G / 2], l2[LS_G / 2];
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        o2[p] = make_float2(pts.ohi[2 * p], pts.ohi[2 * p + 1]);
+        l2[p] = make_float2(lam[2 * p], lam[2 * p + 1]);
+    }
+    float2 aT = make_float2(0.0f, 0.0f), aB = make_float2(0.0f, 0.0f);
+    if (ok == 0xffffffffu) {
+        far_adj_lines<false>(tl, 0, 32, o2, l2, aT, aB, pts.jg);
+    } else {
+        int i = 0;
+        while (i < 32) {
+            const unsigned rest = ok >> i;
+            if (rest & 1u) {
+                const unsigned zeros = ~rest;
+                const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
+                far_adj_lines<false>(tl, i, j, o2, l2, aT, aB, pts.jg);
+                i = j;
+            } else {
+                far_adj_lines<true>(tl, i, i + 1, o2, l2, aT, aB, pts.jg);
+                ++i;
+            }
+        }
+    }
+    accT += aT.x + aT.y;
+    accB += aB.x + aB.y;
+}
+
+__device__ __forceinline__ void chunk_fp64_adj(const AdjTile<double>& tl, const WarpPoints<double>& pts,
+                                               const double (&lam)[LS_G], double half_invT, double& accT,
+                                               double& accB)
+{
+    for (int i = 0; i < 32; ++i) {
+        const double bh = tl.bhi[i];
+        const double4_32a p2 = tl.r2[i];
+        const int2 jr = tl.jr[i];
+        const double aS = tl.aS[i], nn = tl.nn[i];
+#pragma unroll
+        for (int g = 0; g < LS_G; ++g) {
+            if (in_range(pts.jg[g], jr)) {
+                const double x = fabs(pts.ohi[g] - bh) * p2.x;
+                const double a = p2.y;
+                double w4[4];
+                voigt_w_dw<double>(x, 0.0, a, p2.w, w4, nullptr);
+                // H_x = Re w', H_a = -Im w'
+                const double V0 = p2.z * w4[0];
+                const double V1 = p2.z * x * w4[2];
+                const double V2 = -p2.z * a * w4[3];
+                const double Db = -(V0 + V1 + V2);
+                const double ft = aS * V0 + half_invT * Db + nn * V2;
+                accT = fma(lam[g], ft, accT);
+                accB = fma(lam[g], V2, accB);
+            }
+        }
+    }
+}
+
 template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_kernel(
     const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
-    const R* __restrict__ clo, const R* __restrict__ rec3, const float* __restrict__ agg, const double* __restrict__ nu,
-    int64_t N, int64_t nl, int layer0, int ksplit, const double* __restrict__ T, const double* __restrict__ g_sigma,
-    double lam_scale, double* __restrict__ part, int nstrips)
+    const R* __restrict__ rec3, const int2* __restrict__ jnear, const float* __restrict__ agg,
+    const double* __restrict__ nu, int64_t N, int64_t nl, int layer0, int ksplit, const double* __restrict__ T,
+    const double* __restrict__ g_sigma, double lam_scale, double* __restrict__ part, int nstrips)
 {
     using R4 = typename vec4<R>::type;
     __shared__ AdjTile<R> tiles[LS_WARPS];
-    __shared__ float olo_s[LS_WARPS][32 * LS_G];
-    __shared__ R dtab_s[LS_WARPS][32];
     __shared__ double red[2][LS_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
@@ -894,19 +947,17 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
     const R half_invT = (R)(0.5 / T[layer]);
     AdjTile<R>& tl = tiles[w];
-    float* olo = olo_s[w];
 
     double sT = 0.0, sB = 0.0;
     WarpPoints<R> pts;
-    if (pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast, olo)) {
+    if (pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) {
         int64_t cb, ce;
         strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
-        const float cmin = agg[2 * layer], amin = agg[2 * layer + 1];
         const size_t lay = (size_t)nloc * nl;
         const R4* r1g = rec1 + lay;
         const R4* r2g = rec2 + lay;
-        const R* clg = clo + lay;
         const R* r3g = rec3 + 2 * lay;
+        const int2* jng = FAST ? jnear + lay : nullptr;
         R lam[LS_G];
 #pragma unroll
         for (int g = 0; g < LS_G; ++g)
@@ -915,7 +966,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
         LineRec<R> nx;
         R naS = R(0), nnn = R(0);
         if (cb < ce) {
-            nx.load(nu_hat, jrange, r1g, r2g, clg, cb + lane, ce);
+            nx.load(nu_hat, jrange, r1g, r2g, jng, cb + lane, ce);
             if (cb + lane < ce) {
                 naS = r3g[2 * (cb + lane)];
                 nnn = r3g[2 * (cb + lane) + 1];
@@ -928,117 +979,39 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                 float bl;
                 Off<R>::make(nx.nu, pts.ref, &bh, &bl);
                 tl.bhi[lane] = bh;
-                tl.blo[lane] = bl;
                 tl.r2[lane] = nx.p2;
-                tl.clo[lane] = nx.cl;
                 tl.jr[lane] = nx.jr;
-                const R G = nx.p1.x, Al = nx.p1.y, F1 = nx.p1.z, F2 = nx.p1.w, aS = naS, nn = nnn;
-                R4 tc, uc;
-                tc.x = Al * (aS + nn);
-                tc.y = aS * F1 + half_invT * R(2) * F1 + nn * (F1 - R(2) * G * Al);
-                tc.z = aS * F2 + half_invT * R(2) * F2 + nn * R(6) * F2;
-                tc.w = nn * (R(-6) * G * F2);
-                uc.x = Al;
-                uc.y = F1 - R(2) * G * Al;
-                uc.z = R(6) * F2;
-                uc.w = R(-6) * G * F2;
-                tl.t[lane] = tc;
-                tl.u[lane] = uc;
-                tl.G[lane] = G;
-                tl.aS[lane] = aS;
-                tl.nn[lane] = nn;
+                tl.jn[lane] = nx.jn;
+                tl.aS[lane] = naS;
+                tl.nn[lane] = nnn;
                 if (FAST) {
-                    const float nbf = -(float)bh, Gf = (float)G;
-                    tl.q0[lane] = make_float4(nbf, nbf, Gf, Gf);
-                    tl.qt0[lane] = make_float4((float)tc.x, (float)tc.x, (float)tc.y, (float)tc.y);
-                    tl.qt1[lane] = make_float4((float)tc.z, (float)tc.z, (float)tc.w, (float)tc.w);
-                    tl.qu0[lane] = make_float4((float)uc.x, (float)uc.x, (float)uc.y, (float)uc.y);
-                    tl.qu1[lane] = make_float4((float)uc.z, (float)uc.z, (float)uc.w, (float)uc.w);
+                    // fast-form coefficients from G, Al, F1 = 1.5 B Al, F2 = -2 G B Al
+                    const float G = (float)nx.p1.x, Al = (float)nx.p1.y, F1 = (float)nx.p1.z, F2 = (float)nx.p1.w;
+                    const float aS = (float)naS, nn = (float)nnn, hT = (float)half_invT;
+                    const float T1 = Al * (aS + nn);
+                    const float T2 = aS * F1 + hT * 2.0f * F1 + nn * (F1 - 2.0f * G * Al);
+                    const float T3 = aS * F2 + hT * 2.0f * F2 + nn * 6.0f * F2;
+                    const float T4 = nn * (-6.0f * G * F2);
+                    const float U1 = Al, U2 = F1 - 2.0f * G * Al, U3 = 6.0f * F2, U4 = -6.0f * G * F2;
+                    const float nb = -(float)bh;
+                    tl.q0[lane] = make_float4(nb, nb, G, G);
+                    tl.qt0[lane] = make_float4(T1, T1, T2, T2);
+                    tl.qt1[lane] = make_float4(T3, T3, T4, T4);
+                    tl.qu0[lane] = make_float4(U1, U1, U2, U2);
+                    tl.qu1[lane] = make_float4(U3, U3, U4, U4);
                 }
             }
             __syncwarp();
             if (t0 + 32 < ce) {
                 int64_t l = t0 + 32 + lane;
-                nx.load(nu_hat, jrange, r1g, r2g, clg, l, ce);
+                nx.load(nu_hat, jrange, r1g, r2g, jng, l, ce);
                 naS = (l < ce) ? r3g[2 * l] : R(0);
                 nnn = (l < ce) ? r3g[2 * l + 1] : R(0);
             }
-            bool fast = false;
-            if (FAST) {
-                bool incut = (tl.jr[31].x <= pts.jw0) && (tl.jr[0].y >= pts.jw1);
-                fast = incut && all_far((float)tl.bhi[0], (float)tl.bhi[31], (float)pts.ow0, (float)pts.ow1, cmin,
-                                        amin, (float)Tier<R>::z2_fast_adj);
-            }
-            if (fast) {
-                fast_adj<R>(tl, pts.ohi, lam, accT, accB);
-            } else {
-                for (int i = 0; i < 32; ++i) {
-                    const R bh = tl.bhi[i];
-                    const R4 p2 = tl.r2[i];
-                    const int2 jr = tl.jr[i];
-                    bool line_far = false;
-                    if (FAST)
-                        line_far = all_far((float)bh, (float)bh, (float)pts.ow0, (float)pts.ow1, (float)p2.x,
-                                           (float)p2.y, (float)Tier<R>::z2_fast_adj);
-                    if (line_far) {
-                        const R G = tl.G[i];
-                        const R4 tc = tl.t[i];
-                        const R4 uc = tl.u[i];
-                        const bool full = (jr.x <= pts.jw0) && (jr.y >= pts.jw1);
-#pragma unroll
-                        for (int g = 0; g < LS_G; ++g) {
-                            R d = pts.ohi[g] - bh;
-                            R rho = rcp_fast(fma(d, d, G));
-                            R lm = (full || (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y)) ? lam[g] : R(0);
-                            R lr = lm * rho;
-                            accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
-                            accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
-                        }
-                    } else {
-                        const float bl = tl.blo[i];
-                        const R cl = tl.clo[i];
-                        const R aS = tl.aS[i], nn = tl.nn[i];
-                        R* dtab = dtab_s[w];
-                        if (FAST) {
-                            const R hn = R(lane + 1) * (R)Tier<R>::h;
-                            __syncwarp();
-                            dtab[lane] = rcp_fast(fma(hn, hn, p2.y * p2.y));
-                            __syncwarp();
-                        }
-#pragma unroll
-                        for (int g = 0; g < LS_G; ++g) {
-                            if (pts.jg[g] >= jr.x && pts.jg[g] <= jr.y) {
-                                R dh, dl, x, xl;
-                                Off<R>::dnu2(pts.ohi[g], olo[g * 32 + lane], bh, bl, &dh, &dl);
-                                scaled_pair(dh, dl, p2.x, cl, &x, &xl);
-                                R a = p2.y;
-                                if (FAST && fma(x, x, a * a) >= (R)Tier<R>::z2_fast_adj) {
-                                    const R G = tl.G[i];
-                                    const R4 tc = tl.t[i];
-                                    const R4 uc = tl.u[i];
-                                    R d = dh + dl;
-                                    R rho = rcp_fast(fma(d, d, G));
-                                    R lr = lam[g] * rho;
-                                    accT = fma(lr, fma(rho, fma(rho, fma(rho, tc.w, tc.z), tc.y), tc.x), accT);
-                                    accB = fma(lr, fma(rho, fma(rho, fma(rho, uc.w, uc.z), uc.y), uc.x), accB);
-                                    continue;
-                                }
-                                R w4[4];
-                                voigt_w_dw<R>(x, xl, a, p2.w, w4, FAST ? dtab : nullptr);
-                                const R wr = w4[0], dr = w4[2], di = w4[3];
-                                // H_x = Re w', H_a = -Im w'
-                                R V0 = p2.z * wr;
-                                R V1 = p2.z * x * dr;
-                                R V2 = -p2.z * a * di;
-                                R Db = -(V0 + V1 + V2);
-                                R ft = aS * V0 + half_invT * Db + nn * V2;
-                                accT = fma(lam[g], ft, accT);
-                                accB = fma(lam[g], V2, accB);
-                            }
-                        }
-                    }
-                }
-            }
+            if constexpr (FAST)
+                chunk_far_adj(tl, pts, lam, accT, accB);
+            else
+                chunk_fp64_adj(tl, pts, lam, half_invT, accT, accB);
             sT += (double)accT;
             sB += (double)accB;
             accT = R(0);
@@ -1068,11 +1041,13 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     }
 }
 
-// g_T[n] = sum over (strip, chunk) partials; g_b = sum over layers (fixed order).
-__global__ void adjoint_reduce_kernel(const double* __restrict__ part, int L, int per_layer, double unscale,
-                                      double inv_sb, double* __restrict__ g_T, double* __restrict__ g_b)
+// g_T[n] = sum over the main kernel's (strip, chunk) partials and the near
+// kernel's block partials; g_b = sum over layers (fixed order).
+__global__ void adjoint_reduce_kernel(const double* __restrict__ part, int L, int per_layer,
+                                      const double* __restrict__ part_near, int per_layer_near, double inv_sb,
+                                      double* __restrict__ g_T, double* __restrict__ g_b)
 {
-    __shared__ double red[256];
+    __shared__ double red[2][256];
     double gb = 0.0;
     for (int n = 0; n < L; ++n) {
         double a = 0.0, b = 0.0;
@@ -1080,24 +1055,28 @@ __global__ void adjoint_reduce_kernel(const double* __restrict__ part, int L, in
             a += part[2 * ((size_t)n * per_layer + i)];
             b += part[2 * ((size_t)n * per_layer + i) + 1];
         }
-        red[threadIdx.x] = a;
+        if (part_near)
+            for (int i = threadIdx.x; i < per_layer_near; i += blockDim.x) {
+                a += part_near[2 * ((size_t)n * per_layer_near + i)];
+                b += part_near[2 * ((size_t)n * per_layer_near + i) + 1];
+            }
+        red[0][threadIdx.x] = a;
+        red[1][threadIdx.x] = b;
         __syncthreads();
         for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+            if (threadIdx.x < s) {
+                red[0][threadIdx.x] += red[0][threadIdx.x + s];
+                red[1][threadIdx.x] += red[1][threadIdx.x + s];
+            }
             __syncthreads();
         }
-        if (threadIdx.x == 0) g_T[n] = red[0] * unscale;
-        __syncthreads();
-        red[threadIdx.x] = b;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            g_T[n] = red[0][0];
+            gb += red[1][0];
         }
-        if (threadIdx.x == 0) gb += red[0];
         __syncthreads();
     }
-    if (threadIdx.x == 0) g_b[0] = gb * unscale * inv_sb;
+    if (threadIdx.x == 0) g_b[0] = gb * inv_sb;
 }
 
 } // namespace xsd
@@ -1111,6 +1090,7 @@ namespace {
 size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 
 int strips_of(int64_t N) { return (int)((N + LS_STRIP - 1) / LS_STRIP); }
+int near_blocks(int64_t N) { return (int)((N + NR_THREADS - 1) / NR_THREADS); }
 
 // split the line window of each strip so that the grid holds enough CTAs
 int choose_ksplit(int64_t nl, int64_t N, int Lc)
@@ -1126,36 +1106,38 @@ int choose_ksplit(int64_t nl, int64_t N, int Lc)
 
 struct XsPlan {
     int prec, Lc, ksplit, nchunks;
-    size_t off_jr, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_part, total;
+    size_t off_jr, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_jn, off_near, off_part, off_npart, total;
 };
 
-XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc, bool adjoint)
+XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
 {
     XsPlan p;
     p.prec = prec;
     p.Lc = Lc;
-    size_t rs = (prec == XS_PREC_FP64) ? sizeof(double) : sizeof(float);
+    const bool mixed = (prec == XS_PREC_MIXED);
+    const size_t rs = mixed ? sizeof(float) : sizeof(double);
+    const size_t n1 = (size_t)std::max<int64_t>(nl, 1);
     p.ksplit = choose_ksplit(nl, N, Lc);
     size_t off = 0;
-    p.off_jr = off;
-    off += align256(sizeof(int2) * (size_t)std::max<int64_t>(nl, 1));
-    p.off_agg = off;
-    off += align256(sizeof(float) * 2 * (size_t)L);
-    p.off_rec1 = off;
-    off += align256(4 * rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
-    p.off_rec2 = off;
-    off += align256(4 * rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
-    p.off_rec3 = off;
-    off += align256(2 * rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
-    p.off_clo = off;
-    off += align256(rs * (size_t)std::max<int64_t>(nl, 1) * Lc);
-    p.off_part = off;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off += align256(bytes);
+        return o;
+    };
+    p.off_jr = take(sizeof(int2) * n1);
+    p.off_agg = take(sizeof(float) * 2 * (size_t)L);
+    p.off_rec1 = take(4 * rs * n1 * Lc);
+    p.off_rec2 = take(4 * rs * n1 * Lc);
+    p.off_rec3 = take(2 * rs * n1 * Lc);
+    p.off_clo = take(rs * n1 * Lc);
+    p.off_jn = take(mixed ? sizeof(int2) * n1 * Lc : 0);
+    p.off_near = take(mixed ? sizeof(double) * (size_t)Lc * N : 0);
     size_t fwd_part = (p.ksplit > 1) ? sizeof(double) * (size_t)p.ksplit * Lc * N : 0;
     size_t adj_part = sizeof(double) * 2 * (size_t)L * strips_of(N) * p.ksplit;
-    off += align256(std::max(fwd_part, adj_part));
+    p.off_part = take(std::max(fwd_part, adj_part));
+    p.off_npart = take(mixed ? sizeof(double) * 2 * (size_t)L * near_blocks(N) : 0);
     p.total = off;
     p.nchunks = (L + Lc - 1) / Lc;
-    (void)adjoint;
     return p;
 }
 
@@ -1164,13 +1146,13 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc, bool adjoint)
 size_t xs_workspace_bytes(int64_t n_lines, int64_t N, int32_t L, int prec)
 {
     if (n_lines < 0 || N <= 0 || L <= 0) return 0;
-    return plan_xs(n_lines, N, L, prec, L, true).total;
+    return plan_xs(n_lines, N, L, prec, L).total;
 }
 
 size_t xs_workspace_min_bytes(int64_t n_lines, int64_t N, int32_t L, int prec)
 {
     if (n_lines < 0 || N <= 0 || L <= 0) return 0;
-    return plan_xs(n_lines, N, L, prec, 1, true).total;
+    return plan_xs(n_lines, N, L, prec, 1).total;
 }
 
 namespace xsi {
@@ -1179,7 +1161,7 @@ static int pick_plan(int64_t nl, int64_t N, int32_t L, int prec, size_t ws_bytes
 {
     int Lc = L;
     while (true) {
-        XsPlan p = plan_xs(nl, N, L, prec, Lc, true);
+        XsPlan p = plan_xs(nl, N, L, prec, Lc);
         if (p.total <= ws_bytes) {
             *out = p;
             return XS_OK;
@@ -1197,28 +1179,32 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
     // flags: XS_RUN_KEEP_ADJ  (forward) also write the adjoint's per-line records
     //        XS_RUN_REUSE     (adjoint) the records of an immediately preceding forward
     //                         with the same inputs and workspace are still valid
+    constexpr bool FAST = std::is_same<R, float>::value;
     const bool reuse = adjoint && (flags & XS_RUN_REUSE) && p.nchunks == 1;
     const bool want_rec3 = adjoint || (flags & XS_RUN_KEEP_ADJ);
     using R4 = typename vec4<R>::type;
     const int64_t nl = ln->n;
-    const bool mixed = (p.prec == XS_PREC_MIXED);
-    const double scale = mixed ? MIXED_SCALE : 1.0;
-    const double unscale = mixed ? MIXED_UNSCALE : 1.0;
+    const double scale = FAST ? MIXED_SCALE : 1.0;
+    const double unscale = FAST ? MIXED_UNSCALE : 1.0;
     int2* jr = (int2*)(ws + p.off_jr);
     float* agg = (float*)(ws + p.off_agg);
     R4* rec1 = (R4*)(ws + p.off_rec1);
     R4* rec2 = (R4*)(ws + p.off_rec2);
     R* rec3 = (R*)(ws + p.off_rec3);
     R* clo = (R*)(ws + p.off_clo);
+    int2* jn = FAST ? (int2*)(ws + p.off_jn) : nullptr;
+    double* near = FAST ? (double*)(ws + p.off_near) : nullptr;
     double* part = (double*)(ws + p.off_part);
+    double* npart = FAST ? (double*)(ws + p.off_npart) : nullptr;
     const int strips = strips_of(N);
+    const int nblk = near_blocks(N);
 
     if (nl == 0) {
         if (adjoint) {
             if (cudaMemsetAsync(g_T, 0, sizeof(double) * L, st) != cudaSuccess) return XS_ECUDA;
             if (cudaMemsetAsync(g_b, 0, sizeof(double), st) != cudaSuccess) return XS_ECUDA;
         } else {
-            size_t es = mixed ? sizeof(float) : sizeof(double);
+            size_t es = FAST ? sizeof(float) : sizeof(double);
             if (cudaMemsetAsync(sigma, 0, es * (size_t)L * N, st) != cudaSuccess) return XS_ECUDA;
         }
         return XS_OK;
@@ -1235,35 +1221,46 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
             dim3 pg((unsigned)((nl + 255) / 256), (unsigned)lc);
             line_params_kernel<R><<<pg, 256, 0, st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp,
                                                        nl, ln->mass_amu, ln->q_exponent, T, P, l0, sb, scale, rec1,
-                                                       rec2, clo, want_rec3 ? rec3 : nullptr, agg);
+                                                       rec2, clo, want_rec3 ? rec3 : nullptr, agg, nu, N, jr, jn);
             count_launch();
         }
         dim3 grid((unsigned)strips, (unsigned)lc, (unsigned)p.ksplit);
-        R4* r1b = rec1;
-        R4* r2b = rec2;
-        R* r3b = rec3;
+        dim3 ngrid((unsigned)nblk, (unsigned)lc);
         if (!adjoint) {
+            if (FAST) {
+                near_sum_kernel<<<ngrid, NR_THREADS, 0, st>>>(ln->nu_hat, nl, (const float4*)rec2, (const float*)clo,
+                                                              jn, agg, nu, N, l0, near);
+                count_launch();
+            }
             prof_begin(0, st);
-            linesum_kernel<R, std::is_same<R, float>::value><<<grid, LS_THREADS, 0, st>>>(
-                ln->nu_hat, jr, r1b, r2b, clo, agg, nu, N, nl, l0, p.ksplit, unscale, sigma, mixed ? 1 : 0, part, lc);
+            linesum_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, jr, rec1, rec2, jn, agg, nu, N, nl, l0,
+                                                                 p.ksplit, unscale, sigma, FAST ? 1 : 0, part, lc,
+                                                                 near);
             prof_end(0, st);
             count_launch();
             if (p.ksplit > 1) {
                 count_launch();
                 int64_t cnt = (int64_t)lc * N;
                 combine_kernel<<<(unsigned)((cnt + 255) / 256), 256, 0, st>>>(part, p.ksplit, cnt, (int64_t)l0 * N,
-                                                                              cnt, unscale, sigma, mixed ? 1 : 0);
+                                                                              cnt, unscale, sigma, FAST ? 1 : 0);
             }
         } else {
             prof_begin(1, st);
-            linesum_adjoint_kernel<R, std::is_same<R, float>::value><<<grid, LS_THREADS, 0, st>>>(
-                ln->nu_hat, jr, r1b, r2b, clo, r3b, agg, nu, N, nl, l0, p.ksplit, T, g_sigma, unscale, part, strips);
+            linesum_adjoint_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, jr, rec1, rec2, rec3, jn, agg,
+                                                                         nu, N, nl, l0, p.ksplit, T, g_sigma,
+                                                                         unscale, part, strips);
             prof_end(1, st);
             count_launch();
+            if (FAST) {
+                near_adjoint_kernel<<<ngrid, NR_THREADS, 0, st>>>(ln->nu_hat, nl, (const float4*)rec2,
+                                                                  (const float*)clo, (const float*)rec3, jn, agg, nu,
+                                                                  N, l0, T, g_sigma, unscale, npart);
+                count_launch();
+            }
         }
     }
     if (adjoint) {
-        adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit, 1.0, 1.0 / sb, g_T, g_b);
+        adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit, npart, nblk, 1.0 / sb, g_T, g_b);
         count_launch();
     }
     return (cudaGetLastError() == cudaSuccess) ? XS_OK : XS_ECUDA;
