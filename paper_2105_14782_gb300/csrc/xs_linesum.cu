@@ -836,10 +836,10 @@ struct AdjTile {
 };
 
 // packed K = 1 adjoint over lines [i0, i1); MASKED: per (line, point) by far_point
+// per point sums of f_T and f_b (lambda is applied once per chunk by the caller)
 template <bool MASKED>
 __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
-                                              const float2 (&l2)[LS_G / 2], float2& aT, float2& aB,
-                                              const int (&jg)[LS_G])
+                                              float2 (&aT)[LS_G / 2], float2 (&aB)[LS_G / 2], const int (&jg)[LS_G])
 {
 #pragma unroll 2
     for (int i = i0; i < i1; ++i) {
@@ -854,15 +854,14 @@ __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, 
         for (int p = 0; p < LS_G / 2; ++p) {
             float2 d = __fadd2_rn(o2[p], nb);
             float2 rho = rcp2(__ffma2_rn(d, d, G));
-            float2 lr = __fmul2_rn(l2[p], rho);
-            if (MASKED) {
-                lr.x = far_point(jg[2 * p], cut, nr) ? lr.x : 0.0f;
-                lr.y = far_point(jg[2 * p + 1], cut, nr) ? lr.y : 0.0f;
-            }
             float2 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
             float2 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
-            aT = __ffma2_rn(lr, pt, aT);
-            aB = __ffma2_rn(lr, pu, aB);
+            if (MASKED) {
+                rho.x = far_point(jg[2 * p], cut, nr) ? rho.x : 0.0f;
+                rho.y = far_point(jg[2 * p + 1], cut, nr) ? rho.y : 0.0f;
+            }
+            aT[p] = __ffma2_rn(rho, pt, aT[p]);
+            aB[p] = __ffma2_rn(rho, pu, aB[p]);
         }
     }
 }
@@ -872,15 +871,15 @@ __device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const Wa
 {
     const int lane = threadIdx.x & 31;
     const unsigned ok = __ballot_sync(0xffffffffu, covers_far(tl.jr[lane], tl.jn[lane], pts.jw0, pts.jw1));
-    float2 o2[LS_G / 2], l2[LS_G / 2];
+    float2 o2[LS_G / 2], aT[LS_G / 2], aB[LS_G / 2];
 #pragma unroll
     for (int p = 0; p < LS_G / 2; ++p) {
         o2[p] = make_float2(pts.ohi[2 * p], pts.ohi[2 * p + 1]);
-        l2[p] = make_float2(lam[2 * p], lam[2 * p + 1]);
+        aT[p] = make_float2(0.0f, 0.0f);
+        aB[p] = make_float2(0.0f, 0.0f);
     }
-    float2 aT = make_float2(0.0f, 0.0f), aB = make_float2(0.0f, 0.0f);
     if (ok == 0xffffffffu) {
-        far_adj_lines<false>(tl, 0, 32, o2, l2, aT, aB, pts.jg);
+        far_adj_lines<false>(tl, 0, 32, o2, aT, aB, pts.jg);
     } else {
         int i = 0;
         while (i < 32) {
@@ -888,16 +887,19 @@ __device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const Wa
             if (rest & 1u) {
                 const unsigned zeros = ~rest;
                 const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
-                far_adj_lines<false>(tl, i, j, o2, l2, aT, aB, pts.jg);
+                far_adj_lines<false>(tl, i, j, o2, aT, aB, pts.jg);
                 i = j;
             } else {
-                far_adj_lines<true>(tl, i, i + 1, o2, l2, aT, aB, pts.jg);
+                far_adj_lines<true>(tl, i, i + 1, o2, aT, aB, pts.jg);
                 ++i;
             }
         }
     }
-    accT += aT.x + aT.y;
-    accB += aB.x + aB.y;
+#pragma unroll
+    for (int p = 0; p < LS_G / 2; ++p) {
+        accT = fmaf(lam[2 * p], aT[p].x, fmaf(lam[2 * p + 1], aT[p].y, accT));
+        accB = fmaf(lam[2 * p], aB[p].x, fmaf(lam[2 * p + 1], aB[p].y, accB));
+    }
 }
 
 __device__ __forceinline__ void chunk_fp64_adj(const AdjTile<double>& tl, const WarpPoints<double>& pts,

@@ -1,0 +1,426 @@
+"""Continuous-batching server for forward + gradient requests of the emission model.
+
+Many HMC chains send requests of uneven size (line count, grid size, layer count).
+Line lists stay resident on the device (a pool registered once); each admitted
+request gets a slot (its own CUDA stream) and a contiguous region of one
+preallocated device arena holding its workspace and buffers.  Requests are
+admitted in arrival order as slots and arena memory free up (a request that does
+not fit lets smaller ones behind it go first, up to a bounded skip), so work of
+several requests overlaps on the GPU.  Completion is detected by polling CUDA
+events; every wait is bounded.
+
+The scheduling core (Arena, Scheduler) is plain host code and runs with any
+executor; `LibxsExecutor` launches the work through libxs (xs_model_logl_grad).
+"""
+from __future__ import annotations
+
+import bisect
+import ctypes as C
+import heapq
+import itertools
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+import workloads as W
+
+ALIGN = 256
+
+# request status
+PENDING, RUNNING, DONE, REJECTED, FAILED, CANCELLED = "pending", "running", "done", "rejected", "failed", "cancelled"
+
+
+def _align(v):
+    return (int(v) + ALIGN - 1) // ALIGN * ALIGN
+
+
+class Arena:
+    """First-fit allocator over [0, size) bytes with coalescing free list."""
+
+    def __init__(self, size: int, fail_hook=None):
+        self.size = int(size)
+        self.free = [(0, self.size)]  # sorted (offset, length)
+        self.used = 0
+        self.fail_hook = fail_hook  # callable(nbytes) -> bool, True makes alloc fail (fault injection)
+
+    def alloc(self, nbytes: int):
+        n = _align(nbytes)
+        if self.fail_hook is not None and self.fail_hook(n):
+            return None
+        for i, (off, ln) in enumerate(self.free):
+            if ln >= n:
+                if ln == n:
+                    self.free.pop(i)
+                else:
+                    self.free[i] = (off + n, ln - n)
+                self.used += n
+                return off, n
+        return None
+
+    def release(self, block):
+        off, n = block
+        i = bisect.bisect_left(self.free, (off, 0))
+        self.free.insert(i, (off, n))
+        # coalesce with neighbours
+        if i + 1 < len(self.free) and self.free[i][0] + self.free[i][1] == self.free[i + 1][0]:
+            self.free[i] = (self.free[i][0], self.free[i][1] + self.free[i + 1][1])
+            self.free.pop(i + 1)
+        if i > 0 and self.free[i - 1][0] + self.free[i - 1][1] == self.free[i][0]:
+            self.free[i - 1] = (self.free[i - 1][0], self.free[i - 1][1] + self.free[i][1])
+            self.free.pop(i)
+        self.used -= n
+
+    def largest_free(self):
+        return max((ln for _, ln in self.free), default=0)
+
+
+@dataclass
+class Request:
+    rid: int
+    chain: int
+    n_lines: int
+    n_grid: int
+    n_layers: int
+    theta: np.ndarray
+    t_submit: float = 0.0
+    t_start: float = 0.0
+    t_done: float = 0.0
+    status: str = PENDING
+    nbytes: int = 0
+    block: tuple = None
+    slot: int = -1
+    result: np.ndarray = None  # [logL, dlogL/dtheta...]
+    error: str = ""
+    evals: int = 0
+    handle: object = None
+
+    @property
+    def latency(self):
+        return self.t_done - self.t_submit
+
+
+class Scheduler:
+    """Admission by slots and arena memory, completion by polling the executor."""
+
+    def __init__(self, executor, arena_bytes: int, slots: int, max_skip: int = 8, clock=time.perf_counter):
+        self.ex = executor
+        self.arena = Arena(arena_bytes, fail_hook=getattr(executor, "fail_hook", None))
+        self.slots = [None] * slots
+        self.queue = []  # FIFO of pending requests
+        self.max_skip = max_skip
+        self.clock = clock
+        self.done = []
+        self.counts = {"admitted": 0, "rejected": 0, "failed": 0, "cancelled": 0, "completed": 0}
+
+    def submit(self, req: Request):
+        req.t_submit = self.clock()
+        req.nbytes = self.ex.bytes_needed(req)
+        if req.nbytes <= 0 or req.nbytes > self.arena.size or not self.ex.valid(req):
+            req.status = REJECTED
+            req.error = "invalid request" if req.nbytes <= 0 or not self.ex.valid(req) else "exceeds device budget"
+            req.t_done = req.t_submit
+            self.counts["rejected"] += 1
+            self.done.append(req)
+            return req
+        req.status = PENDING
+        self.queue.append(req)
+        return req
+
+    def cancel(self, req: Request) -> bool:
+        if req.status == PENDING and req in self.queue:
+            self.queue.remove(req)
+            req.status = CANCELLED
+            req.t_done = self.clock()
+            self.counts["cancelled"] += 1
+            self.done.append(req)
+            return True
+        return False
+
+    def _admit(self):
+        progressed = False
+        i = 0
+        while i < len(self.queue) and i <= self.max_skip:
+            free = [k for k, s in enumerate(self.slots) if s is None]
+            if not free:
+                break
+            req = self.queue[i]
+            block = self.arena.alloc(req.nbytes)
+            if block is None:
+                i += 1  # let a smaller request behind it try (bounded skip)
+                continue
+            self.queue.pop(i)
+            k = free[0]
+            req.block, req.slot, req.status = block, k, RUNNING
+            req.t_start = self.clock()
+            try:
+                req.handle = self.ex.launch(req, block, k)
+            except Exception as e:  # launch failure: free and report, others unaffected
+                self.arena.release(block)
+                req.status, req.error, req.t_done = FAILED, str(e), self.clock()
+                self.counts["failed"] += 1
+                self.done.append(req)
+                continue
+            self.slots[k] = req
+            self.counts["admitted"] += 1
+            progressed = True
+        return progressed
+
+    def _poll(self):
+        progressed = False
+        for k, req in enumerate(self.slots):
+            if req is not None and self.ex.ready(req):
+                try:
+                    req.result = self.ex.collect(req)
+                    req.status = DONE
+                    self.counts["completed"] += 1
+                except Exception as e:
+                    req.status, req.error = FAILED, str(e)
+                    self.counts["failed"] += 1
+                req.t_done = self.clock()
+                self.arena.release(req.block)
+                self.slots[k] = None
+                self.done.append(req)
+                progressed = True
+        return progressed
+
+    def step(self):
+        a = self._poll()
+        b = self._admit()
+        return a or b
+
+    def busy(self):
+        return bool(self.queue) or any(s is not None for s in self.slots)
+
+    def drain(self, timeout_s: float = 600.0):
+        t0 = self.clock()
+        while self.busy():
+            if not self.step():
+                time.sleep(0.0002)
+            if self.clock() - t0 > timeout_s:
+                raise TimeoutError("drain timed out")
+
+
+# ------------------------------------------------------------------ libxs executor
+
+
+class LinePool:
+    """Water-like line lists of log-spaced sizes, sorted and resident on the device."""
+
+    SIZES = (1000, 3000, 10_000, 30_000, 100_000, 300_000, 1_000_000)
+
+    def __init__(self, device="cuda", sizes=SIZES, seed=W.SEED_SERVE):
+        from . import xs
+        self.sizes = list(sizes)
+        hosts = {n: W.water_like(n, seed=seed + i) for i, n in enumerate(self.sizes)}
+        co = W.co_like(2000, seed=seed + 100)
+        self.lists = {n: xs.DeviceLines(h, device) for n, h in hosts.items()}
+        self.co = xs.DeviceLines(co, device)
+        # sum over lines of the fraction of a full-band log grid inside each line's
+        # wing cut: in-cut pairs of an N-point grid ~ fraction * N (for reporting)
+        ref = W.grid_lognu(200_001)
+        def frac(c):
+            return float(np.sum(np.searchsorted(ref, c + 25.0, "right") - np.searchsorted(ref, c - 25.0, "left"))) / ref.size
+        self._frac = {n: frac(np.sort(h.nu_hat)) for n, h in hosts.items()}
+        self.co_fraction = frac(np.sort(co.nu_hat))
+
+    def cut_fraction(self, n):
+        return self._frac[n]
+
+    def nearest(self, n):
+        return min(self.sizes, key=lambda s: abs(math.log(s) - math.log(max(n, 1))))
+
+
+class LibxsExecutor:
+    """Runs a request as xs_model_logl_grad on its slot's stream, inside its arena
+    block: [model workspace | grid | P | dP | d_obs | sig_obs | out]."""
+
+    def __init__(self, pool: LinePool, arena_tensor, streams, prec=1, fail_hook=None):
+        import torch
+        from . import xs
+        self.torch, self.xs = torch, xs
+        self.pool = pool
+        self.arena_t = arena_tensor
+        self.base = arena_tensor.data_ptr()
+        self.streams = streams
+        self.prec = prec
+        self.fail_hook = fail_hook
+        self.lib = xs.lib()
+
+    def valid(self, r):
+        return r.n_lines >= 1 and 2 <= r.n_grid <= 2_000_000 and 1 <= r.n_layers <= 1000 and np.all(np.isfinite(r.theta))
+
+    def _model(self, r, ptrs=None):
+        xs = self.xs
+        lines = [self.pool.lists[self.pool.nearest(r.n_lines)], self.pool.co]
+        sp = (xs.XsLinesC * xs.MAX_SPECIES)()
+        for i, s in enumerate(lines):
+            sp[i] = s.struct()
+        p = ptrs or {}
+        return xs.XsModelC(2, sp, p.get("nu"), r.n_grid, p.get("P"), p.get("dP"), r.n_layers, 25.0, 1e5, 2.313, 1e-8,
+                           p.get("d"), p.get("s"), self.prec)
+
+    def _layout(self, r):
+        # sizing only: the model check wants non-null buffers, any device address will do
+        m = self._model(r, {k: self.base for k in ("nu", "P", "dP", "d", "s")})
+        ws = self.lib.xs_model_workspace_bytes(C.byref(m))
+        N, L = r.n_grid, r.n_layers
+        parts = [("ws", ws), ("nu", 8 * N), ("P", 8 * L), ("dP", 8 * L), ("d", 8 * N), ("s", 8 * N), ("out", 8 * 8)]
+        off, lay = 0, {}
+        for k, n in parts:
+            lay[k] = (off, n)
+            off += _align(n)
+        return lay, off
+
+    def bytes_needed(self, r):
+        if not self.valid(r):
+            return -1
+        return self._layout(r)[1]
+
+    def launch(self, r, block, slot):
+        torch = self.torch
+        lay, _ = self._layout(r)
+        off0 = block[0]
+        ptr = {k: self.base + off0 + o for k, (o, n) in lay.items()}
+        st = self.streams[slot]
+        # request inputs from the host (pinned), copied on the slot's stream
+        N, L = r.n_grid, r.n_layers
+        nu = W.grid_lognu(N)
+        P, dP = W.pressure_layers(L)
+        host = torch.from_numpy(np.concatenate([nu, P, dP, np.ones(N), np.full(N, 0.01)])).pin_memory()
+        sizes = [N, L, L, N, N]
+        with torch.cuda.stream(st):
+            o = 0
+            for key, n in zip(("nu", "P", "dP", "d", "s"), sizes):
+                dst = self.arena_t.narrow(0, off0 + lay[key][0], 8 * n).view(torch.float64)
+                dst.copy_(host[o:o + n], non_blocking=True)
+                o += n
+        m = self._model(r, ptr)
+        th = (C.c_double * 5)(*[float(v) for v in r.theta])
+        code = self.lib.xs_model_logl_grad(C.byref(m), th, C.c_void_p(ptr["out"]), None, C.c_void_p(ptr["ws"]),
+                                           lay["ws"][1], C.c_void_p(st.cuda_stream))
+        if code != 0:
+            raise RuntimeError(f"xs_model_logl_grad: {code}")
+        out_h = torch.empty(6, dtype=torch.float64).pin_memory()
+        with torch.cuda.stream(st):
+            out_h.copy_(self.arena_t.narrow(0, off0 + lay["out"][0], 48).view(torch.float64), non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        r.evals = 2 * L * (self.pool.cut_fraction(self.pool.nearest(r.n_lines)) * N + self.pool.co_fraction * N)
+        return (ev, out_h, host)
+
+    def ready(self, r):
+        return r.handle[0].query()
+
+    def collect(self, r):
+        out = r.handle[1].numpy().copy()
+        if not np.all(np.isfinite(out)):
+            raise RuntimeError("non-finite result")
+        return out
+
+
+# ------------------------------------------------------------------ closed-loop HMC load
+
+
+def request_stream(n, seed=W.SEED_SERVE):
+    nl, ng, nlay = W.serving_requests(n, seed)
+    th = W.theta_points(n, seed + 1)
+    return [Request(rid=i, chain=-1, n_lines=int(nl[i]), n_grid=int(ng[i]), n_layers=int(nlay[i]), theta=th[i])
+            for i in range(n)]
+
+
+def closed_loop(sched: Scheduler, chains: int, offered_rate: float, duration_s: float, seed=W.SEED_SERVE,
+                timeout_s: float = 900.0, cancel_at_end: bool = False):
+    """`chains` HMC chains, each with at most one request outstanding; after its
+    result a chain thinks Exp(mean chains/offered_rate) before the next one, so the
+    offered rate is `offered_rate` when the server keeps up.  With
+    `cancel_at_end`, requests still queued when the window closes are cancelled
+    (the running ones finish), which bounds the drain of a saturated server."""
+    rng = np.random.default_rng(seed + 7)
+    reqs = iter(request_stream(100_000, seed))
+    think = chains / offered_rate
+    t0 = sched.clock()
+    wake = [(t0 + rng.exponential(think), c) for c in range(chains)]
+    heapq.heapify(wake)
+    outstanding = {}
+    finished = []
+    nd = 0
+    while True:
+        now = sched.clock()
+        if now - t0 > timeout_s:
+            raise TimeoutError("closed loop timed out")
+        while wake and wake[0][0] <= now and now - t0 < duration_s:
+            _, c = heapq.heappop(wake)
+            r = next(reqs)
+            r.chain = c
+            sched.submit(r)
+            outstanding[r.rid] = r
+        if cancel_at_end and now - t0 >= duration_s and sched.queue:
+            for r in list(sched.queue):
+                sched.cancel(r)
+        progressed = sched.step()
+        for r in sched.done[nd:]:
+            nd += 1
+            if r.rid in outstanding:
+                del outstanding[r.rid]
+                finished.append(r)
+                if r.status != CANCELLED:
+                    heapq.heappush(wake, (sched.clock() + rng.exponential(think), r.chain))
+        if sched.clock() - t0 >= duration_s and not outstanding:
+            break
+        if not progressed:
+            time.sleep(0.0002)
+    return finished, sched.clock() - t0
+
+
+def open_loop(sched: Scheduler, rate: float, duration_s: float, seed=W.SEED_SERVE, timeout_s: float = 900.0):
+    """Poisson arrivals at `rate` req/s for `duration_s`, then drain."""
+    rng = np.random.default_rng(seed + 9)
+    reqs = iter(request_stream(100_000, seed + 1))
+    t0 = sched.clock()
+    t_next = t0 + rng.exponential(1.0 / rate)
+    sent = []
+    while True:
+        now = sched.clock()
+        if now - t0 > timeout_s:
+            raise TimeoutError("open loop timed out")
+        while t_next <= now and t_next - t0 < duration_s:
+            r = next(reqs)
+            r.chain = len(sent)
+            sched.submit(r)
+            sent.append(r)
+            t_next += rng.exponential(1.0 / rate)
+        progressed = sched.step()
+        if now - t0 >= duration_s and not sched.busy():
+            break
+        if not progressed:
+            time.sleep(0.0002)
+    return sent, sched.clock() - t0
+
+
+def mean_request_evals(pool: LinePool, n=100_000, seed=W.SEED_SERVE):
+    """Expected Voigt evaluations (forward + adjoint) of one request of the stream."""
+    nl, ng, nlay = W.serving_requests(n, seed)
+    fr = np.array([pool.cut_fraction(pool.nearest(int(v))) for v in nl]) + pool.co_fraction
+    return float(np.mean(2.0 * nlay * ng * fr))
+
+
+def summarize(finished, wall_s):
+    ok = [r for r in finished if r.status == DONE]
+    lat = np.array([r.latency for r in ok]) if ok else np.array([np.nan])
+    return {"completed": len(ok), "rejected": sum(r.status == REJECTED for r in finished),
+            "failed": sum(r.status == FAILED for r in finished),
+            "cancelled": sum(r.status == CANCELLED for r in finished), "req_per_s": len(ok) / wall_s,
+            "evals_per_s": sum(r.evals for r in ok) / wall_s,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(np.mean(lat)), "wall_s": wall_s}
+
+
+def make_server(arena_bytes=int(40e9), slots=4, prec=1, device="cuda", fail_hook=None, pool=None):
+    import torch
+    pool = pool or LinePool(device)
+    arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
+    streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
+    ex = LibxsExecutor(pool, arena, streams, prec=prec, fail_hook=fail_hook)
+    return Scheduler(ex, int(arena_bytes), slots), pool
