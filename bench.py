@@ -235,6 +235,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison forward")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--layers", type=int, default=100,
+                    help="layer count of the emission workload (100; fewer only for small profiling cases)")
     ap.add_argument("--serve-seconds", type=float, nargs=2, default=(15.0, 30.0),
                     help="closed-loop and open-loop windows of the serving measurement")
     args = ap.parse_args()
@@ -259,7 +261,7 @@ def main():
     from paper_2105_14782_gb300 import xs
 
     prec = xs.PREC_MIXED if args.prec == "mixed" else xs.PREC_FP64
-    atm = W.emission_case()
+    atm = W.emission_case(n_layers=args.layers)
     L, N = len(atm.p_bar), len(atm.nu)
     triples = sum(in_cut_triples(sp, atm.nu, atm.wing_cut, L) for sp in atm.species)
     evals_per_step = 2 * triples  # forward + adjoint evaluation of every in-cut triple
@@ -404,7 +406,7 @@ def main():
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == xs.PREC_MIXED else "f64",
                 "data": "synthetic",
-                "config": {"workload": "emission: 100 layers 1e-3..1e2 bar, 200,000 water-like + 20,000 CO-like "
+                "config": {"workload": f"emission: {L} layers 1e-3..1e2 bar, 200,000 water-like + 20,000 CO-like "
                                        "lines, 20,000-point log grid 4340-4390 cm^-1, W = 25 cm^-1",
                            "step": "forward + gradient (logL and dlogL/dtheta, theta = T0, alpha, 2 log10 VMR, "
                                    "broadening scale)",

@@ -37,7 +37,7 @@ constexpr int LS_WARPS = 4;
 constexpr int LS_G = 8;
 constexpr int LS_STRIP = LS_WARPS * 32 * LS_G; // 1024
 // resident CTAs per SM the register budget targets (FP32: 96 registers; FP64 keeps more)
-template <class R> struct MinBlocks { static constexpr int v = 5; };
+template <class R> struct MinBlocks { static constexpr int v = 4; }; // 128 registers: ILP over occupancy
 template <> struct MinBlocks<double> { static constexpr int v = 3; };
 // the near/far boundary of the FP32 path: pairs at |z| < NEAR_Z go to the near kernels
 constexpr double NEAR_Z = 25.0;
@@ -48,11 +48,18 @@ constexpr double NEAR_Z = 25.0;
 // nu_j - nu_hat <= W (double precision, boundary included).  Both are
 // non-decreasing along a sorted line list.
 __global__ void cut_range_kernel(const double* __restrict__ nu_hat, int64_t nl, const double* __restrict__ nu,
-                                 int64_t N, double W, int2* __restrict__ jr)
+                                 int64_t N, double W, int2* __restrict__ jr, float2* __restrict__ nuf)
 {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
     double c = nu_hat[l];
+    if (nuf) {
+        // centre relative to the first grid point as hi + lo floats, so that the
+        // FP32 kernels form line offsets without FP64 arithmetic
+        const double o = c - nu[0];
+        const float h = (float)o;
+        nuf[l] = make_float2(h, (float)(o - (double)h));
+    }
     int64_t lo = 0, hi = N; // first j with nu[j] - c >= -W
     while (lo < hi) {
         int64_t m = (lo + hi) >> 1;
@@ -300,12 +307,18 @@ struct WarpPoints {
     int jw0, jw1; // first and last valid point of the warp
     R ow0, ow1;   // their offsets
     double ref;
+    float rh, rl; // ref - nu[0] as hi + lo floats
 
     __device__ bool init(const double* nu, int64_t jbase, int64_t jlast)
     {
         const int lane = threadIdx.x & 31;
         if (jbase > jlast) return false;
         ref = nu[min64(jlast, jbase + 16 * LS_G)];
+        {
+            const double o = ref - nu[0];
+            rh = (float)o;
+            rl = (float)(o - (double)rh);
+        }
 #pragma unroll
         for (int g = 0; g < LS_G; ++g) {
             int64_t j = jbase + g * 32 + lane;
@@ -482,15 +495,18 @@ __device__ __forceinline__ void chunk_fp64(const LineTile<double>& tl, const War
 // one lane's line record as loaded from global memory
 template <class R>
 struct LineRec {
-    double nu;
+    double nu;  // centre (FP64 path)
+    float2 nf;  // centre - nu[0] as hi + lo floats (FP32 path)
     typename vec4<R>::type p1, p2;
     int2 jr, jn;
 
-    __device__ void load(const double* nu_hat, const int2* jrange, const typename vec4<R>::type* rec1,
-                         const typename vec4<R>::type* rec2, const int2* jnear, int64_t l, int64_t ce)
+    __device__ void load(const double* nu_hat, const float2* nuf, const int2* jrange,
+                         const typename vec4<R>::type* rec1, const typename vec4<R>::type* rec2, const int2* jnear,
+                         int64_t l, int64_t ce)
     {
+        constexpr bool FAST = std::is_same<R, float>::value;
         if (l < ce) {
-            nu = nu_hat[l];
+            if (FAST) nf = nuf[l]; else nu = nu_hat[l];
             p1 = rec1[l];
             p2 = rec2[l];
             jr = jrange[l];
@@ -498,7 +514,7 @@ struct LineRec {
         } else {
             // padding: the chunk's last line with zero amplitude keeps every
             // chunk test and offset that of real lines
-            nu = nu_hat[ce - 1];
+            if (FAST) nf = nuf[ce - 1]; else nu = nu_hat[ce - 1];
             jr = jrange[ce - 1];
             jn = jnear ? jnear[ce - 1] : make_int2(1, 0);
             p1.x = R(1); p1.y = R(0); p1.z = R(0); p1.w = R(0);
@@ -507,9 +523,21 @@ struct LineRec {
     }
 };
 
+// Offset of a line's centre to the warp's reference point: FP32 from the float
+// pairs (the difference of the hi parts is exact or within half an ulp of the
+// result, the lo parts add the rest), FP64 on the FP64 path.
+__device__ __forceinline__ void line_offset(const LineRec<float>& r, const WarpPoints<float>& pts, float* bh)
+{
+    *bh = (r.nf.x - pts.rh) + (r.nf.y - pts.rl);
+}
+__device__ __forceinline__ void line_offset(const LineRec<double>& r, const WarpPoints<double>& pts, double* bh)
+{
+    *bh = r.nu;
+}
+
 template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
-    const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
+    const double* __restrict__ nu_hat, const float2* __restrict__ nuf, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
     const int2* __restrict__ jnear, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N,
     int64_t nl, int layer0, int ksplit, double unscale, void* __restrict__ sigma, int sigma_is_float,
@@ -542,13 +570,12 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
         slo[g] = R(0);
     }
     LineRec<R> nx;
-    if (cb < ce) nx.load(nu_hat, jrange, r1g, r2g, jng, cb + lane, ce);
+    if (cb < ce) nx.load(nu_hat, nuf, jrange, r1g, r2g, jng, cb + lane, ce);
 
     for (int64_t t0 = cb; t0 < ce; t0 += 32) {
         {
             R bh;
-            float bl;
-            Off<R>::make(nx.nu, pts.ref, &bh, &bl);
+            line_offset(nx, pts, &bh);
             tl.bhi[lane] = bh;
             tl.r2[lane] = nx.p2;
             tl.jr[lane] = nx.jr;
@@ -565,7 +592,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
             }
         }
         __syncwarp();
-        if (t0 + 32 < ce) nx.load(nu_hat, jrange, r1g, r2g, jng, t0 + 32 + lane, ce); // in flight meanwhile
+        if (t0 + 32 < ce) nx.load(nu_hat, nuf, jrange, r1g, r2g, jng, t0 + 32 + lane, ce); // in flight meanwhile
 
         if constexpr (FAST)
             chunk_far(tl, pts, cmin, amin, acc);
@@ -933,7 +960,7 @@ __device__ __forceinline__ void chunk_fp64_adj(const AdjTile<double>& tl, const 
 
 template <class R, bool FAST>
 __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_kernel(
-    const double* __restrict__ nu_hat, const int2* __restrict__ jrange,
+    const double* __restrict__ nu_hat, const float2* __restrict__ nuf, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
     const R* __restrict__ rec3, const int2* __restrict__ jnear, const float* __restrict__ agg,
     const double* __restrict__ nu, int64_t N, int64_t nl, int layer0, int ksplit, const double* __restrict__ T,
@@ -941,7 +968,6 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
 {
     using R4 = typename vec4<R>::type;
     __shared__ AdjTile<R> tiles[LS_WARPS];
-    __shared__ double red[2][LS_WARPS];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int strip = blockIdx.x, nloc = blockIdx.y, kc = blockIdx.z;
     const int layer = layer0 + nloc;
@@ -968,7 +994,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
         LineRec<R> nx;
         R naS = R(0), nnn = R(0);
         if (cb < ce) {
-            nx.load(nu_hat, jrange, r1g, r2g, jng, cb + lane, ce);
+            nx.load(nu_hat, nuf, jrange, r1g, r2g, jng, cb + lane, ce);
             if (cb + lane < ce) {
                 naS = r3g[2 * (cb + lane)];
                 nnn = r3g[2 * (cb + lane) + 1];
@@ -978,8 +1004,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
         for (int64_t t0 = cb; t0 < ce; t0 += 32) {
             {
                 R bh;
-                float bl;
-                Off<R>::make(nx.nu, pts.ref, &bh, &bl);
+                line_offset(nx, pts, &bh);
                 tl.bhi[lane] = bh;
                 tl.r2[lane] = nx.p2;
                 tl.jr[lane] = nx.jr;
@@ -1006,7 +1031,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
             __syncwarp();
             if (t0 + 32 < ce) {
                 int64_t l = t0 + 32 + lane;
-                nx.load(nu_hat, jrange, r1g, r2g, jng, l, ce);
+                nx.load(nu_hat, nuf, jrange, r1g, r2g, jng, l, ce);
                 naS = (l < ce) ? r3g[2 * l] : R(0);
                 nnn = (l < ce) ? r3g[2 * l + 1] : R(0);
             }
@@ -1021,25 +1046,16 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
             __syncwarp();
         }
     }
-    // fixed-order block reduction
+    // fixed-order warp reduction; one partial per warp (no block barrier, so a
+    // warp that finishes early does not hold the block's slot)
     for (int o = 16; o > 0; o >>= 1) {
         sT += __shfl_xor_sync(0xffffffffu, sT, o);
         sB += __shfl_xor_sync(0xffffffffu, sB, o);
     }
     if (lane == 0) {
-        red[0][w] = sT;
-        red[1][w] = sB;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0;
-        for (int i = 0; i < LS_WARPS; ++i) {
-            a += red[0][i];
-            b += red[1][i];
-        }
-        size_t o = ((size_t)layer * nstrips + strip) * ksplit + kc;
-        part[2 * o] = a;
-        part[2 * o + 1] = b;
+        const size_t o = (((size_t)layer * nstrips + strip) * ksplit + kc) * LS_WARPS + w;
+        part[2 * o] = sT;
+        part[2 * o + 1] = sB;
     }
 }
 
@@ -1108,7 +1124,8 @@ int choose_ksplit(int64_t nl, int64_t N, int Lc)
 
 struct XsPlan {
     int prec, Lc, ksplit, nchunks;
-    size_t off_jr, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_jn, off_near, off_part, off_npart, total;
+    size_t off_jr, off_nuf, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_jn, off_near, off_part, off_npart,
+        total;
 };
 
 XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
@@ -1127,6 +1144,7 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
         return o;
     };
     p.off_jr = take(sizeof(int2) * n1);
+    p.off_nuf = take(mixed ? sizeof(float2) * n1 : 0);
     p.off_agg = take(sizeof(float) * 2 * (size_t)L);
     p.off_rec1 = take(4 * rs * n1 * Lc);
     p.off_rec2 = take(4 * rs * n1 * Lc);
@@ -1135,7 +1153,7 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
     p.off_jn = take(mixed ? sizeof(int2) * n1 * Lc : 0);
     p.off_near = take(mixed ? sizeof(double) * (size_t)Lc * N : 0);
     size_t fwd_part = (p.ksplit > 1) ? sizeof(double) * (size_t)p.ksplit * Lc * N : 0;
-    size_t adj_part = sizeof(double) * 2 * (size_t)L * strips_of(N) * p.ksplit;
+    size_t adj_part = sizeof(double) * 2 * (size_t)L * strips_of(N) * p.ksplit * LS_WARPS;
     p.off_part = take(std::max(fwd_part, adj_part));
     p.off_npart = take(mixed ? sizeof(double) * 2 * (size_t)L * near_blocks(N) : 0);
     p.total = off;
@@ -1189,6 +1207,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
     const double scale = FAST ? MIXED_SCALE : 1.0;
     const double unscale = FAST ? MIXED_UNSCALE : 1.0;
     int2* jr = (int2*)(ws + p.off_jr);
+    float2* nuf = FAST ? (float2*)(ws + p.off_nuf) : nullptr;
     float* agg = (float*)(ws + p.off_agg);
     R4* rec1 = (R4*)(ws + p.off_rec1);
     R4* rec2 = (R4*)(ws + p.off_rec2);
@@ -1212,7 +1231,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
         return XS_OK;
     }
     if (!reuse) {
-        cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr);
+        cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr, nuf);
         layer_agg_init_kernel<<<(2 * L + 255) / 256, 256, 0, st>>>(agg, 2 * L);
         count_launch(2);
     }
@@ -1235,7 +1254,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
                 count_launch();
             }
             prof_begin(0, st);
-            linesum_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, jr, rec1, rec2, jn, agg, nu, N, nl, l0,
+            linesum_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, nuf, jr, rec1, rec2, jn, agg, nu, N, nl, l0,
                                                                  p.ksplit, unscale, sigma, FAST ? 1 : 0, part, lc,
                                                                  near);
             prof_end(0, st);
@@ -1248,7 +1267,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
             }
         } else {
             prof_begin(1, st);
-            linesum_adjoint_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, jr, rec1, rec2, rec3, jn, agg,
+            linesum_adjoint_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, nuf, jr, rec1, rec2, rec3, jn, agg,
                                                                          nu, N, nl, l0, p.ksplit, T, g_sigma,
                                                                          unscale, part, strips);
             prof_end(1, st);
@@ -1262,7 +1281,8 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
         }
     }
     if (adjoint) {
-        adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit, npart, nblk, 1.0 / sb, g_T, g_b);
+        adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit * LS_WARPS, npart, nblk, 1.0 / sb, g_T,
+                                                  g_b);
         count_launch();
     }
     return (cudaGetLastError() == cudaSuccess) ? XS_OK : XS_ECUDA;
