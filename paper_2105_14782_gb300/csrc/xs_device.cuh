@@ -348,40 +348,120 @@ __device__ __forceinline__ void faddeeva_d(R x, R xl, R a, R Kc, R* wr, R* wi, R
     }
 }
 
-// Out-of-line entry points for the per-point tiered evaluation, so the hot
-// loops that call them stay small in the instruction cache.
-// Series-only entry (FP32 line sum, |z| < 8): Re w.
-static __device__ __noinline__ float voigt_H_series(float x, float xl, float a, float Kc, const float* dtab)
+// ------------------------------------------------------------------ wing polynomials
+//
+// The asymptotic series of Eq. asywofz, truncated after the term k = ASY_K, as a
+// polynomial in u = 1/|z|^2 with per-line coefficients (FP32 near kernels,
+// 6 <= |z| < 25).  Term k is c_k Re(i z^-(2k+1))/sqrt(pi) = c_k Im(z^(2k+1)) u^(2k+1)/sqrt(pi),
+// c_k = (2k-1)!!/2^k.  Writing z^m = x alpha_m + i beta_m with alpha_m, beta_m
+// homogeneous polynomials in r = |z|^2 and a (x^2 = r - a^2), multiplication by
+// z^2 = (r - 2a^2) + 2iax gives
+//   alpha_{m+2} = (r - 2a^2) alpha_m - 2a beta_m,   beta_{m+2} = (r - 2a^2) beta_m + 2a (r - a^2) alpha_m,
+// alpha_1 = 1, beta_1 = a.  With beta_{2k+1} = a r^k sum_j q_kj t^j (t = a^2/r):
+//   H = sum_n C_n u^(n+1),  C_n = (a/sqrt(pi)) sum_{k+j=n} c_k q_kj a^(2j).
+// For the adjoint, Euler's relation for the homogeneous terms (degree -(2k+1))
+// gives H + x H_x + a H_a = -sum_k 2k T_k, and differentiating a^(2j+1) u^p at
+// fixed x gives
+//   a H_a = sum_n E_n u^(n+1) - 2 a^2 sum_n (n+1) C_n u^(n+2),  E_n = (1/sqrt(pi)) sum_{k+j=n} (2j+1) c_k q_kj a^(2j+1).
+// With ASY_K = 6 the truncation and FP32 rounding stay below 4e-7 of H for |z| >= 6.
+// To keep every coefficient inside the FP32 range (a up to 25, scaled strengths
+// up to ~1e13) the polynomials are written in v = ASY_S u (v < 1 for |z| >= 6):
+// the table holds c_k q_kj / ASY_S^k and a^(2j) enters as (a^2/ASY_S)^j, so that
+// H = u sum_n C'_n v^n with C'_n = C_n / ASY_S^n (a power of two: exact).
+constexpr int ASY_K = 6;
+constexpr int ASY_N = 2 * ASY_K + 1; // powers u^1 .. u^13
+constexpr float ASY_S = 32.0f;
+
+struct AsyTable {
+    float cq[ASY_K + 1][ASY_K + 1]; // c_k q_kj / ASY_S^k (j <= k)
+};
+
+constexpr AsyTable make_asy_table()
 {
-    float wr, wi;
-    w_series_rec(x, xl, a, Kc, dtab, &wr, &wi);
-    return wr;
+    // integer coefficients b[s] of beta_m = sum_s b[s] r^s a^(m-2s) and c[s] of
+    // alpha_m = sum_s c[s] r^s a^(m-1-2s), advanced m -> m + 2
+    long long b[ASY_K + 2] = {}, c[ASY_K + 2] = {};
+    b[0] = 1;
+    c[0] = 1;
+    AsyTable t{};
+    double ck = 1.0;
+    for (int k = 0; k <= ASY_K; ++k) {
+        if (k > 0) {
+            long long nb[ASY_K + 2] = {}, nc[ASY_K + 2] = {};
+            for (int s = 0; s <= k; ++s) {
+                const long long bs1 = s > 0 ? b[s - 1] : 0, cs1 = s > 0 ? c[s - 1] : 0;
+                nc[s] = cs1 - 2 * c[s] - 2 * b[s];
+                nb[s] = bs1 - 2 * b[s] + 2 * cs1 - 2 * c[s];
+            }
+            for (int s = 0; s <= k; ++s) {
+                b[s] = nb[s];
+                c[s] = nc[s];
+            }
+            ck *= (2.0 * k - 1.0) / 2.0;
+        }
+        // beta_{2k+1} = sum_s b[s] r^s a^(2k+1-2s) = a r^k sum_j b[k-j] t^j
+        double sk = 1.0;
+        for (int i = 0; i < k; ++i) sk /= (double)ASY_S;
+        for (int j = 0; j <= k; ++j) t.cq[k][j] = (float)(ck * (double)b[k - j] * sk);
+    }
+    return t;
 }
 
-// Asymptotic series of Eq. asywofz truncated at K = 5, in real form:
-//   Re w = (a r / sqrt(pi)) sum_{k<=5} sum_{m<=k} W5[k][m] r^k t^m,  r = 1/|z|^2, t = a^2 r,
-// W5[k][m] = c_k q_{k,m} with c_k = (2k-1)!!/2^k and q_k(t) = Im((x+ia)^{2k+1}) / (a |z|^{2k}).
-// Truncation error below 4e-8 of Re w for |z| >= 8.
-__device__ const float W5[6][6] = {{1.0f, 0, 0, 0, 0, 0},
-                                   {1.5f, -2.0f, 0, 0, 0, 0},
-                                   {3.75f, -15.0f, 12.0f, 0, 0, 0},
-                                   {13.125f, -105.0f, 210.0f, -120.0f, 0, 0},
-                                   {59.0625f, -787.5f, 2835.0f, -3780.0f, 1680.0f, 0},
-                                   {324.84375f, -6496.875f, 36382.5f, -83160.0f, 83160.0f, -30240.0f}};
+__constant__ const AsyTable ASY = make_asy_table();
 
-// Coefficient n (0..10) of the same sum written in rho = 1/(dnu^2 + gamma^2) for one line:
-//   Av H = rho sum_n C_n rho^n,  C_n = Al sum_{k+m=n} W5[k][m] B^k G^m   (B = 2 beta^2, G = gamma^2)
-__device__ __forceinline__ float k5_coeff(int n, float Al, float B, float G)
+// C'_n (n = 0 .. ASY_N - 1) of H = u sum_n C'_n v^n, times amp.
+__device__ __forceinline__ void asy_coeffs(float a, float amp, float (&C)[ASY_N])
 {
-    float c = 0.0f;
-    for (int k = (n + 1) / 2; k <= (n < 5 ? n : 5); ++k) {
-        const int m = n - k;
-        float bk = 1.0f, gm = 1.0f;
-        for (int i = 0; i < k; ++i) bk *= B;
-        for (int i = 0; i < m; ++i) gm *= G;
-        c = fmaf(W5[k][m], bk * gm, c);
+    const float a2 = a * a * (1.0f / ASY_S);
+    float ap[ASY_K + 1]; // amp a^(2j+1) / sqrt(pi)
+    ap[0] = amp * a * (float)INV_SQRTPI;
+#pragma unroll
+    for (int j = 1; j <= ASY_K; ++j) ap[j] = ap[j - 1] * a2;
+#pragma unroll
+    for (int n = 0; n < ASY_N; ++n) C[n] = 0.0f;
+#pragma unroll
+    for (int k = 0; k <= ASY_K; ++k)
+#pragma unroll
+        for (int j = 0; j <= k; ++j) C[k + j] = fmaf(ASY.cq[k][j], ap[j], C[k + j]);
+}
+
+// Adjoint: f_T = u sum_n F_n v^n and f_b = u sum_n G_n v^n (n = 0 .. ASY_N) for
+// f_T = aS V0 + hT D_beta + nn D_gamma and f_b = D_gamma, with V0 = amp H,
+// D_beta = -amp (H + x H_x + a H_a), D_gamma = amp a H_a.
+__device__ __forceinline__ void asy_coeffs_adj(float a, float amp, float aS, float hT, float nn,
+                                               float (&F)[ASY_N + 1], float (&G)[ASY_N + 1])
+{
+    const float a2 = a * a * (1.0f / ASY_S); // a^2 / ASY_S
+    float ap[ASY_K + 1];
+    ap[0] = amp * a * (float)INV_SQRTPI;
+#pragma unroll
+    for (int j = 1; j <= ASY_K; ++j) ap[j] = ap[j - 1] * a2;
+    float C[ASY_N], D[ASY_N], E[ASY_N];
+#pragma unroll
+    for (int n = 0; n < ASY_N; ++n) {
+        C[n] = 0.0f;
+        D[n] = 0.0f;
+        E[n] = 0.0f;
     }
-    return Al * c;
+#pragma unroll
+    for (int k = 0; k <= ASY_K; ++k)
+#pragma unroll
+        for (int j = 0; j <= k; ++j) {
+            const float v = ASY.cq[k][j] * ap[j];
+            C[k + j] += v;
+            D[k + j] = fmaf(2.0f * (float)k, v, D[k + j]);
+            E[k + j] = fmaf(2.0f * (float)j + 1.0f, v, E[k + j]);
+        }
+    // coefficient of u v^n: V0: C'_n, D_beta: D'_n, D_gamma: E'_n - 2 (a^2/ASY_S) n C'_{n-1}
+#pragma unroll
+    for (int n = 0; n <= ASY_N; ++n) {
+        const float cn = n < ASY_N ? C[n] : 0.0f;
+        const float dn = n < ASY_N ? D[n] : 0.0f;
+        const float en = n < ASY_N ? E[n] : 0.0f;
+        const float gm = en - (n > 0 ? 2.0f * a2 * (float)n * C[n - 1] : 0.0f);
+        G[n] = gm;
+        F[n] = fmaf(aS, cn, fmaf(hT, dn, nn * gm));
+    }
 }
 
 template <class R>

@@ -656,8 +656,70 @@ struct NearTile {
     float bhi[32], blo[32], clo[32];
     float4 r2[32]; // c, a, Av, Kc
     int2 jn[32];
-    float aS[32], nn[32];
+    float4 hc[32][4]; // Av C_0 .. Av C_12 of the wing polynomial (6 <= |z| < 25)
 };
+
+struct NearAdjTile {
+    float bhi[32], blo[32], clo[32];
+    float4 r2[32];
+    int2 jn[32];
+    float aS[32], nn[32];
+    float4 hf[32][4], hg[32][4]; // f_T and f_b wing polynomials (6 <= |z| < 25)
+};
+
+// |z|^2 from which the near kernels take the wing polynomial in u = 1/|z|^2;
+// below it the series.
+constexpr float NEAR_POLY_Z2 = 36.0f;
+
+// u sum_{n<13} C'_n v^n, v = ASY_S u, by Horner from four float4 of coefficients
+__device__ __forceinline__ float horner13(const float4* h, float u)
+{
+    const float v = ASY_S * u;
+    const float4 h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3];
+    float p = h3.x;
+    p = fmaf(p, v, h2.w);
+    p = fmaf(p, v, h2.z);
+    p = fmaf(p, v, h2.y);
+    p = fmaf(p, v, h2.x);
+    p = fmaf(p, v, h1.w);
+    p = fmaf(p, v, h1.z);
+    p = fmaf(p, v, h1.y);
+    p = fmaf(p, v, h1.x);
+    p = fmaf(p, v, h0.w);
+    p = fmaf(p, v, h0.z);
+    p = fmaf(p, v, h0.y);
+    p = fmaf(p, v, h0.x);
+    return p * u;
+}
+// u sum_{n<14} F_n v^n
+__device__ __forceinline__ float horner14(const float4* h, float u)
+{
+    const float v = ASY_S * u;
+    const float4 h0 = h[0], h1 = h[1], h2 = h[2], h3 = h[3];
+    float p = h3.y;
+    p = fmaf(p, v, h3.x);
+    p = fmaf(p, v, h2.w);
+    p = fmaf(p, v, h2.z);
+    p = fmaf(p, v, h2.y);
+    p = fmaf(p, v, h2.x);
+    p = fmaf(p, v, h1.w);
+    p = fmaf(p, v, h1.z);
+    p = fmaf(p, v, h1.y);
+    p = fmaf(p, v, h1.x);
+    p = fmaf(p, v, h0.w);
+    p = fmaf(p, v, h0.z);
+    p = fmaf(p, v, h0.y);
+    p = fmaf(p, v, h0.x);
+    return p * u;
+}
+
+__device__ __forceinline__ void store16(float4* dst, const float* v, int n)
+{
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        dst[q] = make_float4(4 * q < n ? v[4 * q] : 0.0f, 4 * q + 1 < n ? v[4 * q + 1] : 0.0f,
+                             4 * q + 2 < n ? v[4 * q + 2] : 0.0f, 4 * q + 3 < n ? v[4 * q + 3] : 0.0f);
+}
 
 // Candidate lines of a warp's 32 points: centres within sqrt(625 - a^2)/c < 25/cmin
 // of any of them (binary search on the sorted centres), cut to chunks of 32.
@@ -719,9 +781,16 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
             const float bh = (float)o;
             tl.bhi[lane] = bh;
             tl.blo[lane] = (float)(o - (double)bh);
-            tl.r2[lane] = rec2[lay + l];
+            const float4 p2 = rec2[lay + l];
+            tl.r2[lane] = p2;
             tl.clo[lane] = clo[lay + l];
-            tl.jn[lane] = jnear[lay + l];
+            const int2 nr = jnear[lay + l];
+            tl.jn[lane] = nr;
+            if (nr.x <= nr.y) {
+                float C[ASY_N];
+                asy_coeffs(p2.y, p2.z, C);
+                store16(tl.hc[lane], C, ASY_N);
+            }
         } else {
             tl.jn[lane] = make_int2(1, 0);
         }
@@ -733,9 +802,15 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
                 const float4 p2 = tl.r2[i];
                 float x, xl;
                 scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
-                float wr, wi;
-                faddeeva<float>(x, xl, p2.y, p2.w, &wr, &wi);
-                const float v = p2.z * wr;
+                const float z2 = fmaf(x, x, p2.y * p2.y);
+                float v;
+                if (z2 >= NEAR_POLY_Z2) {
+                    v = horner13(tl.hc[i], rcp_fast(z2));
+                } else {
+                    float wr, wi;
+                    faddeeva<float>(x, xl, p2.y, p2.w, &wr, &wi);
+                    v = p2.z * wr;
+                }
                 const float t = sum + v;
                 comp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
                 sum = t;
@@ -753,7 +828,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
     const double* __restrict__ nu, int64_t N, int layer0, const double* __restrict__ T,
     const double* __restrict__ g_sigma, double lam_scale, double* __restrict__ part)
 {
-    __shared__ NearTile tiles[NR_THREADS / 32];
+    __shared__ NearAdjTile tiles[NR_THREADS / 32];
     __shared__ double red[2][NR_THREADS / 32];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nloc = blockIdx.y;
@@ -771,7 +846,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
         const float half_invT = (float)(0.5 / T[layer]);
         const float lam = (j <= jl) ? (float)(g_sigma[(size_t)layer * N + j] * lam_scale) : 0.0f;
         const size_t lay = (size_t)nloc * nl;
-        NearTile& tl = tiles[w];
+        NearAdjTile& tl = tiles[w];
         int64_t cb, ce;
         near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
         float aT = 0.0f, aB = 0.0f;
@@ -783,11 +858,20 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
                 const float bh = (float)o;
                 tl.bhi[lane] = bh;
                 tl.blo[lane] = (float)(o - (double)bh);
-                tl.r2[lane] = rec2[lay + l];
+                const float4 p2 = rec2[lay + l];
+                tl.r2[lane] = p2;
                 tl.clo[lane] = clo[lay + l];
-                tl.jn[lane] = jnear[lay + l];
-                tl.aS[lane] = rec3[2 * (lay + l)];
-                tl.nn[lane] = rec3[2 * (lay + l) + 1];
+                const int2 nr = jnear[lay + l];
+                tl.jn[lane] = nr;
+                const float aS = rec3[2 * (lay + l)], nn = rec3[2 * (lay + l) + 1];
+                tl.aS[lane] = aS;
+                tl.nn[lane] = nn;
+                if (nr.x <= nr.y) {
+                    float F[ASY_N + 1], G[ASY_N + 1];
+                    asy_coeffs_adj(p2.y, p2.z, aS, half_invT, nn, F, G);
+                    store16(tl.hf[lane], F, ASY_N + 1);
+                    store16(tl.hg[lane], G, ASY_N + 1);
+                }
             } else {
                 tl.jn[lane] = make_int2(1, 0);
             }
@@ -800,16 +884,25 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
                     float x, xl;
                     scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
                     const float a = p2.y;
-                    float wr, wi, dr, di;
-                    faddeeva_d<float>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
-                    // H_x = Re w', H_a = -Im w'
-                    const float V0 = p2.z * wr;
-                    const float V1 = p2.z * x * dr;
-                    const float V2 = -p2.z * a * di;
-                    const float Db = -(V0 + V1 + V2);
-                    const float ft = tl.aS[i] * V0 + half_invT * Db + tl.nn[i] * V2;
+                    const float z2 = fmaf(x, x, a * a);
+                    float ft, fb;
+                    if (z2 >= NEAR_POLY_Z2) {
+                        const float u = rcp_fast(z2);
+                        ft = horner14(tl.hf[i], u);
+                        fb = horner14(tl.hg[i], u);
+                    } else {
+                        float wr, wi, dr, di;
+                        faddeeva_d<float>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
+                        // H_x = Re w', H_a = -Im w'
+                        const float V0 = p2.z * wr;
+                        const float V1 = p2.z * x * dr;
+                        const float V2 = -p2.z * a * di;
+                        const float Db = -(V0 + V1 + V2);
+                        ft = tl.aS[i] * V0 + half_invT * Db + tl.nn[i] * V2;
+                        fb = V2;
+                    }
                     aT = fmaf(lam, ft, aT);
-                    aB = fmaf(lam, V2, aB);
+                    aB = fmaf(lam, fb, aB);
                 }
             }
             sT += (double)aT;
