@@ -35,7 +35,7 @@ import workloads as W  # noqa: E402
 FP32_LANES_PER_SM = 128
 N_SM = 152
 SM_MAX_MHZ = 2070.0
-FLOPS_PER_EVAL = {"fwd": 10, "adj": 20}  # packed K = 1 wing form, FP32 flops per evaluation (FFMA = 2, FADD = RCP = 1)
+FLOPS_PER_EVAL = {"fwd": 8, "adj": 12}  # cheapest packed wing forms (FFMA = 2, FADD = RCP = 1): a lower bound per evaluation
 
 
 def in_cut_triples(lines, nu, W_cut, L):

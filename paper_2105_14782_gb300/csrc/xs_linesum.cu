@@ -89,17 +89,18 @@ __global__ void grid_check_kernel(const double* __restrict__ nu, int64_t N, int*
 
 // ------------------------------------------------------------------ K1: line params
 
+// agg[4n .. 4n+3] = {min c, min a, max a, unused} of layer n
 __global__ void layer_agg_init_kernel(float* agg, int n)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) agg[i] = __int_as_float(0x7f800000); // +inf
+    if (i < n) agg[i] = ((i & 3) < 2) ? __int_as_float(0x7f800000) : 0.0f; // +inf for the minima
 }
 
 // Per (layer, line), FP64 math rounded once to R:
 //   rec1 = {G = gamma^2, Al = s gamma/pi, F1 = 1.5 B Al, F2 = -2 G B Al}   (B = 2 beta^2)
 //   rec2 = {c = 1/(sqrt2 beta), a = gamma c, Av = s c / sqrt(pi), Kc = K(a)}
 //   rec3 = {dlnS/dT, -n/T}                                                   (adjoint only)
-// s = S(T) * scale.  Per layer: agg[2n] = min c, agg[2n+1] = min a.
+// s = S(T) * scale.  Per layer: agg[4n .. 4n+2] = min c, min a, max a.
 // e^{-(k h)^2}, k = 1.., for the two series steps (h = 0.7f and h = 0.5)
 __device__ const float KC_E32[10] = {0.612626433f, 0.140858427f, 0.0121551799f, 0.00039366915f, 4.78511947e-06f,
                                      2.18295906e-08f, 3.73757449e-11f, 2.40173736e-14f, 5.79232066e-18f,
@@ -141,7 +142,7 @@ __device__ __forceinline__ double series_K(double a)
 // s = S(T) * scale.  The Boltzmann exponent of S (Eq. Slog) and c are formed in
 // FP64 in both paths; in the FP32 path the factors that only need ~1e-7
 // (stimulated emission, the width's temperature power, K(a)) use FP32.
-// Per layer: agg[2n] = min c, agg[2n+1] = min a.
+// Per layer: agg[4n .. 4n+2] = min c, min a, max a.
 template <class R>
 __global__ void line_params_kernel(const double* __restrict__ nu_hat, const double* __restrict__ ln_S0,
                                    const double* __restrict__ elower, const double* __restrict__ gamma_ref,
@@ -154,7 +155,7 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
 {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int n = blockIdx.y;
-    float cmin = __int_as_float(0x7f800000), amin = cmin;
+    float cmin = __int_as_float(0x7f800000), amin = cmin, amax = 0.0f;
     if (l < nl) {
         const double Tn = T[layer0 + n], Pn = P_bar[layer0 + n];
         const double nuh = nu_hat[l];
@@ -226,15 +227,18 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
         }
         cmin = (float)cr * (1.0f - 1e-6f);
         amin = (float)a * (1.0f - 1e-6f);
+        amax = (float)a * (1.0f + 1e-6f);
     }
     // block min then one atomic per block (positive floats order like their bits)
     for (int o = 16; o > 0; o >>= 1) {
         cmin = fminf(cmin, __shfl_xor_sync(0xffffffffu, cmin, o));
         amin = fminf(amin, __shfl_xor_sync(0xffffffffu, amin, o));
+        amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     }
     if ((threadIdx.x & 31) == 0 && cmin < __int_as_float(0x7f800000)) {
-        atomicMin((int*)&agg[2 * (layer0 + n)], __float_as_int(cmin));
-        atomicMin((int*)&agg[2 * (layer0 + n) + 1], __float_as_int(amin));
+        atomicMin((int*)&agg[4 * (layer0 + n)], __float_as_int(cmin));
+        atomicMin((int*)&agg[4 * (layer0 + n) + 1], __float_as_int(amin));
+        atomicMax((int*)&agg[4 * (layer0 + n) + 2], __float_as_int(amax));
     }
 }
 
@@ -396,8 +400,9 @@ __device__ __forceinline__ float2 rcp2_shared(float2 v)
 // the MUFU pipe (16 ops/clk/SM) against the FP32 pipe (128 lanes/clk/SM)
 __device__ __forceinline__ float2 rcp2_mix(float2 v, int p) { return (p < 2) ? rcp2_shared(v) : rcp2(v); }
 
-// Packed forms over lines [i0, i1) of a tile.  KIND 1: K = 1, unmasked; KIND 2:
-// K = 2, unmasked; KIND 3: K = 2, masked per (line, point) by far_point.
+// Packed forms over lines [i0, i1) of a tile.  KIND 0: rho (k0 + rho k1), unmasked;
+// KIND 1: K = 1, unmasked; KIND 2: K = 2, unmasked; KIND 3: K = 2, masked per
+// (line, point) by far_point.
 template <int KIND>
 __device__ __forceinline__ void far_lines(const LineTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                           float2 (&a2)[LS_G / 2], const int (&jg)[LS_G])
@@ -418,7 +423,9 @@ __device__ __forceinline__ void far_lines(const LineTile<float>& tl, int i0, int
             float2 d = __fadd2_rn(o2[p], nb);
             float2 rho = rcp2_mix(__ffma2_rn(d, d, G), p);
             float2 u;
-            if (KIND == 1)
+            if (KIND == 0)
+                u = __ffma2_rn(rho, k1, k0);
+            else if (KIND == 1)
                 u = __ffma2_rn(__ffma2_rn(f2hi(v3), rho, k1), rho, k0);
             else
                 u = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(f2lo(v3), rho, f2hi(v2)), rho, f2lo(v2)), rho, k1),
@@ -432,9 +439,20 @@ __device__ __forceinline__ void far_lines(const LineTile<float>& tl, int i0, int
     }
 }
 
+// Lower bound of |z|^2 over a chunk's lines (first and last line offsets -b0,
+// -b31 in the tile) and a warp's points: the smallest centre-to-point distance
+// times the layer's smallest c, and the layer's smallest a.
+__device__ __forceinline__ float chunk_z2min(float nb0, float nb31, const WarpPoints<float>& pts, float cmin,
+                                             float amin)
+{
+    const float dist = fmaxf(fmaxf(-nb0 - pts.ow1, pts.ow0 + nb31), 0.0f);
+    const float xm = dist * cmin;
+    return fmaf(xm, xm, amin * amin);
+}
+
 // One 32-line chunk of the FP32 main kernel.
 __device__ __forceinline__ void chunk_far(const LineTile<float>& tl, const WarpPoints<float>& pts, float cmin,
-                                          float amin, float (&acc)[LS_G])
+                                          float amin, float amax, float (&acc)[LS_G])
 {
     const int lane = threadIdx.x & 31;
     const unsigned ok = __ballot_sync(0xffffffffu, covers_far(tl.jr[lane], tl.jn[lane], pts.jw0, pts.jw1));
@@ -446,12 +464,17 @@ __device__ __forceinline__ void chunk_far(const LineTile<float>& tl, const WarpP
     }
     if (ok == 0xffffffffu) {
         // every pair at |z| >= 25; K = 1 suffices when every pair is at |z| >= 100
-        const float dist = fmaxf(fmaxf(-tl.q0[0].x - pts.ow1, pts.ow0 + tl.q0[31].x), 0.0f);
-        const float xm = dist * cmin;
-        if (fmaf(xm, xm, amin * amin) >= 1.0e4f)
-            far_lines<1>(tl, 0, 32, o2, a2, pts.jg);
-        else
+        // (the K = 2 terms are below 4e-8 of the leading one), and its F2 term,
+        // 2 a^2/|z|^4 of the leading one, is dropped where that is below 2e-8
+        const float z2 = chunk_z2min(tl.q0[0].x, tl.q0[31].x, pts, cmin, amin);
+        if (z2 >= 1.0e4f) {
+            if (2.0f * amax * amax <= 2.0e-8f * z2 * z2)
+                far_lines<0>(tl, 0, 32, o2, a2, pts.jg);
+            else
+                far_lines<1>(tl, 0, 32, o2, a2, pts.jg);
+        } else {
             far_lines<2>(tl, 0, 32, o2, a2, pts.jg);
+        }
     } else {
         int i = 0;
         while (i < 32) {
@@ -556,7 +579,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     int64_t cb, ce;
     strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
     const int layer = layer0 + nloc;
-    const float cmin = agg[2 * layer], amin = agg[2 * layer + 1];
+    const float cmin = agg[4 * layer], amin = agg[4 * layer + 1], amax = agg[4 * layer + 2];
     const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
     const R4* r1g = rec1 + lay;
     const R4* r2g = rec2 + lay;
@@ -595,7 +618,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
         if (t0 + 32 < ce) nx.load(nu_hat, nuf, jrange, r1g, r2g, jng, t0 + 32 + lane, ce); // in flight meanwhile
 
         if constexpr (FAST)
-            chunk_far(tl, pts, cmin, amin, acc);
+            chunk_far(tl, pts, cmin, amin, amax, acc);
         else
             chunk_fp64(tl, pts, acc);
 
@@ -767,7 +790,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
     const double ref = nu[jb];
     const double oj = nu[jc] - ref;
     const float ohi = (float)oj, olo = (float)(oj - (double)ohi);
-    const float cmin = agg[2 * (layer0 + nloc)];
+    const float cmin = agg[4 * (layer0 + nloc)];
     const size_t lay = (size_t)nloc * nl;
     NearTile& tl = tiles[w];
     int64_t cb, ce;
@@ -842,7 +865,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
         const double ref = nu[jb];
         const double oj = nu[jc] - ref;
         const float ohi = (float)oj, olo = (float)(oj - (double)ohi);
-        const float cmin = agg[2 * layer];
+        const float cmin = agg[4 * layer];
         const float half_invT = (float)(0.5 / T[layer]);
         const float lam = (j <= jl) ? (float)(g_sigma[(size_t)layer * N + j] * lam_scale) : 0.0f;
         const size_t lay = (size_t)nloc * nl;
@@ -955,9 +978,11 @@ struct AdjTile {
     R aS[32], nn[32];
 };
 
-// packed K = 1 adjoint over lines [i0, i1); MASKED: per (line, point) by far_point
-// per point sums of f_T and f_b (lambda is applied once per chunk by the caller)
-template <bool MASKED>
+// packed K = 1 adjoint over lines [i0, i1); MASKED: per (line, point) by far_point;
+// DEG2: the rho^3 and rho^4 terms dropped (below 1e-6 of the leading one where the
+// caller takes it).  Per point sums of f_T and f_b (lambda is applied once per
+// chunk by the caller).
+template <bool MASKED, bool DEG2 = false>
 __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                               float2 (&aT)[LS_G / 2], float2 (&aB)[LS_G / 2], const int (&jg)[LS_G])
 {
@@ -974,8 +999,14 @@ __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, 
         for (int p = 0; p < LS_G / 2; ++p) {
             float2 d = __fadd2_rn(o2[p], nb);
             float2 rho = rcp2(__ffma2_rn(d, d, G));
-            float2 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
-            float2 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
+            float2 pt, pu;
+            if (DEG2) {
+                pt = __ffma2_rn(f2hi(t0), rho, f2lo(t0));
+                pu = __ffma2_rn(f2hi(u0), rho, f2lo(u0));
+            } else {
+                pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
+                pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
+            }
             if (MASKED) {
                 rho.x = far_point(jg[2 * p], cut, nr) ? rho.x : 0.0f;
                 rho.y = far_point(jg[2 * p + 1], cut, nr) ? rho.y : 0.0f;
@@ -987,7 +1018,8 @@ __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, 
 }
 
 __device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const WarpPoints<float>& pts,
-                                              const float (&lam)[LS_G], float& accT, float& accB)
+                                              const float (&lam)[LS_G], float cmin, float amin, float amax,
+                                              float& accT, float& accB)
 {
     const int lane = threadIdx.x & 31;
     const unsigned ok = __ballot_sync(0xffffffffu, covers_far(tl.jr[lane], tl.jn[lane], pts.jw0, pts.jw1));
@@ -999,7 +1031,13 @@ __device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const Wa
         aB[p] = make_float2(0.0f, 0.0f);
     }
     if (ok == 0xffffffffu) {
-        far_adj_lines<false>(tl, 0, 32, o2, aT, aB, pts.jg);
+        // the rho^3 and rho^4 terms of f_T and f_b come from the F2 term (relative
+        // size up to 12 a^2/|z|^4): dropped where that is below 1e-6
+        const float z2 = chunk_z2min(tl.q0[0].x, tl.q0[31].x, pts, cmin, amin);
+        if (12.0f * amax * amax <= 1.0e-6f * z2 * z2)
+            far_adj_lines<false, true>(tl, 0, 32, o2, aT, aB, pts.jg);
+        else
+            far_adj_lines<false>(tl, 0, 32, o2, aT, aB, pts.jg);
     } else {
         int i = 0;
         while (i < 32) {
@@ -1067,6 +1105,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     const int64_t j0 = (int64_t)strip * LS_STRIP;
     const int64_t jlast = min64(N - 1, j0 + LS_STRIP - 1);
     const R half_invT = (R)(0.5 / T[layer]);
+    const float cmin = agg[4 * layer], amin = agg[4 * layer + 1], amax = agg[4 * layer + 2];
     AdjTile<R>& tl = tiles[w];
 
     double sT = 0.0, sB = 0.0;
@@ -1129,7 +1168,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                 nnn = (l < ce) ? r3g[2 * l + 1] : R(0);
             }
             if constexpr (FAST)
-                chunk_far_adj(tl, pts, lam, accT, accB);
+                chunk_far_adj(tl, pts, lam, cmin, amin, amax, accT, accB);
             else
                 chunk_fp64_adj(tl, pts, lam, half_invT, accT, accB);
             sT += (double)accT;
@@ -1238,7 +1277,7 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
     };
     p.off_jr = take(sizeof(int2) * n1);
     p.off_nuf = take(mixed ? sizeof(float2) * n1 : 0);
-    p.off_agg = take(sizeof(float) * 2 * (size_t)L);
+    p.off_agg = take(sizeof(float) * 4 * (size_t)L);
     p.off_rec1 = take(4 * rs * n1 * Lc);
     p.off_rec2 = take(4 * rs * n1 * Lc);
     p.off_rec3 = take(2 * rs * n1 * Lc);
@@ -1325,7 +1364,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
     }
     if (!reuse) {
         cut_range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, nl, nu, N, W, jr, nuf);
-        layer_agg_init_kernel<<<(2 * L + 255) / 256, 256, 0, st>>>(agg, 2 * L);
+        layer_agg_init_kernel<<<(4 * L + 255) / 256, 256, 0, st>>>(agg, 4 * L);
         count_launch(2);
     }
     for (int c = 0; c < p.nchunks; ++c) {
