@@ -240,15 +240,17 @@ __device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float 
     const float Q[6] = {0.61262643f, 0.22992550f, 0.08629359f, 0.03238694f, 0.012155180f, 0.0045619742f};
     const float x = xh;
     const float a2 = a * a;
-    const int n0 = __float2int_rn(x / h);
+    const int n0 = __float2int_rn(x * (1.0f / h));
     const float delta = fmaf((float)n0, h, -xh) - xl;
-    const float E0 = expf(-delta * delta);
-    const float P = expf(-2.0f * h * delta);
-    const float Pi = 1.0f / P;
-    // powers of R = e^{-4hx} for the E_n^+ = E_n^- R^n
-    const float R4 = expf(-4.0f * h * x);
-    const float R4i = 1.0f / R4;
-    float Rn = expf(-4.0f * h * x * (float)n0);
+    // small arguments (|delta| <= h/2): the fast exponential is within 2 ulp
+    const float E0 = __expf(-delta * delta);
+    const float P = __expf(-2.0f * h * delta);
+    const float Pi = __expf(2.0f * h * delta);
+    // powers of R = e^{-4hx} for the E_n^+ = E_n^- R^n; they matter only where
+    // 4hx is small (x < 1), elsewhere E_n^+ is negligible against E_n^-
+    const float R4 = __expf(-4.0f * h * x);
+    const float R4i = rcp_fast(R4);
+    float Rn = __expf(-4.0f * h * x * (float)n0);
     auto dn = [&](int n) -> float {
         if (dtab != nullptr && n <= 32) return dtab[n - 1];
         float nh = (float)n * h;
@@ -286,7 +288,7 @@ __device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float 
     sincosf(a * x, &sax, &cax);
     const float c2v = 1.0f - 2.0f * sax * sax; // cos 2ax
     const float s2 = 2.0f * sax * cax;         // sin 2ax
-    float sax_a = (a > 0.0f) ? sax / a : x;
+    float sax_a = (a > 0.0f) ? sax * rcp_fast(a) : x;
     float s2_a = 2.0f * sax_a * cax;
     const float hpi = h * (float)(1.0 / PI);
     *wr = ex * (Kc * c2v + 2.0f * hpi * sax * sax_a) + a * hpi * sc;

@@ -678,13 +678,15 @@ constexpr int NR_THREADS = 128;
 struct NearTile {
     float bhi[32], blo[32], clo[32];
     float4 r2[32]; // c, a, Av, Kc
+    float2 xa[32]; // -c bhi, a^2: x to ~1e-7 for the wing polynomial
     int2 jn[32];
-    float4 hc[32][4]; // Av C_0 .. Av C_12 of the wing polynomial (6 <= |z| < 25)
+    float4 hc[32][4]; // Av C'_0 .. Av C'_12 of the wing polynomial (6 <= |z| < 25)
 };
 
 struct NearAdjTile {
     float bhi[32], blo[32], clo[32];
     float4 r2[32];
+    float2 xa[32];
     int2 jn[32];
     float aS[32], nn[32];
     float4 hf[32][4], hg[32][4]; // f_T and f_b wing polynomials (6 <= |z| < 25)
@@ -795,7 +797,8 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
     NearTile& tl = tiles[w];
     int64_t cb, ce;
     near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
-    float sum = 0.0f, comp = 0.0f;
+    const bool live = j <= jl;
+    float shi = 0.0f, slo = 0.0f;
     for (int64_t t0 = cb; t0 < ce; t0 += 32) {
         const int64_t l = t0 + lane;
         __syncwarp();
@@ -806,6 +809,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
             tl.blo[lane] = (float)(o - (double)bh);
             const float4 p2 = rec2[lay + l];
             tl.r2[lane] = p2;
+            tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
             tl.clo[lane] = clo[lay + l];
             const int2 nr = jnear[lay + l];
             tl.jn[lane] = nr;
@@ -819,28 +823,34 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
         }
         __syncwarp();
         const int nt = (int)min64(32, ce - t0);
+        float acc = 0.0f;
         for (int i = 0; i < nt; ++i) {
             const int2 nr = tl.jn[i];
-            if (j <= jl && in_range((int)j, nr)) {
-                const float4 p2 = tl.r2[i];
-                float x, xl;
-                scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
-                const float z2 = fmaf(x, x, p2.y * p2.y);
-                float v;
+            if (live && in_range((int)j, nr)) {
+                // x to FP32 accuracy suffices for the polynomial (a rational
+                // function of x); the series takes the exact pair
+                const float2 xa = tl.xa[i];
+                const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
+                const float z2 = fmaf(xq, xq, xa.y);
                 if (z2 >= NEAR_POLY_Z2) {
-                    v = horner13(tl.hc[i], rcp_fast(z2));
+                    acc += horner13(tl.hc[i], rcp_fast(z2));
                 } else {
+                    const float4 p2 = tl.r2[i];
+                    float x, xl;
+                    scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
                     float wr, wi;
-                    faddeeva<float>(x, xl, p2.y, p2.w, &wr, &wi);
-                    v = p2.z * wr;
+                    w_small<float>(x, xl, p2.y, p2.w, nullptr, &wr, &wi);
+                    acc = fmaf(p2.z, wr, acc);
                 }
-                const float t = sum + v;
-                comp += (fabsf(sum) >= fabsf(v)) ? (sum - t) + v : (v - t) + sum;
-                sum = t;
             }
         }
+        // fold the chunk's FP32 partial into the compensated sum (TwoSum)
+        const float t = shi + acc;
+        const float bb = t - shi;
+        slo += (shi - (t - bb)) + (acc - bb);
+        shi = t;
     }
-    if (j <= jl) near_sum[(size_t)nloc * N + j] = (double)sum + (double)comp;
+    if (live) near_sum[(size_t)nloc * N + j] = (double)shi + (double)slo;
 }
 
 // The adjoint's near pairs: per point, sum of lambda_j (f_T, f_b) (see
@@ -883,6 +893,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
                 tl.blo[lane] = (float)(o - (double)bh);
                 const float4 p2 = rec2[lay + l];
                 tl.r2[lane] = p2;
+                tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
                 tl.clo[lane] = clo[lay + l];
                 const int2 nr = jnear[lay + l];
                 tl.jn[lane] = nr;
@@ -903,20 +914,24 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
             for (int i = 0; i < nt; ++i) {
                 const int2 nr = tl.jn[i];
                 if (j <= jl && in_range((int)j, nr)) {
-                    const float4 p2 = tl.r2[i];
-                    float x, xl;
-                    scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
-                    const float a = p2.y;
-                    const float z2 = fmaf(x, x, a * a);
+                    const float2 xa = tl.xa[i];
+                    const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
+                    const float z2 = fmaf(xq, xq, xa.y);
                     float ft, fb;
                     if (z2 >= NEAR_POLY_Z2) {
                         const float u = rcp_fast(z2);
                         ft = horner14(tl.hf[i], u);
                         fb = horner14(tl.hg[i], u);
                     } else {
-                        float wr, wi, dr, di;
-                        faddeeva_d<float>(x, xl, a, p2.w, &wr, &wi, &dr, &di);
-                        // H_x = Re w', H_a = -Im w'
+                        const float4 p2 = tl.r2[i];
+                        float x, xl;
+                        scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
+                        const float a = p2.y;
+                        float wr, wi;
+                        w_small<float>(x, xl, a, p2.w, nullptr, &wr, &wi);
+                        // w' = -2 z w + 2i/sqrt(pi);  H_x = Re w', H_a = -Im w'
+                        const float dr = -2.0f * (x * wr - a * wi);
+                        const float di = -2.0f * (x * wi + a * wr) + (float)(2.0 * INV_SQRTPI);
                         const float V0 = p2.z * wr;
                         const float V1 = p2.z * x * dr;
                         const float V2 = -p2.z * a * di;
