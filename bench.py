@@ -38,6 +38,22 @@ SM_MAX_MHZ = 2070.0
 FLOPS_PER_EVAL = {"fwd": 8, "adj": 12}  # cheapest packed wing forms (FFMA = 2, FADD = RCP = 1): a lower bound per evaluation
 
 
+# DRAM bytes (read + write) per launch of linesum_adjoint_kernel<float>, averaged over
+# the two species, from one ncu capture of the 20-layer case scaled to 100 layers
+# (the traffic is per layer); valid only for the kernel sources it was taken on.
+TRAFFIC = {"kernel": "linesum_adjoint_kernel<float>", "bytes_per_launch_100_layers": 2.800e9,
+           "sources_sha256": "e22d567ece65ec048c30cc997db3ef35959ccbf8c760de69bd4176824563a821"}
+
+
+def kernel_sources_sha256():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("xs_linesum.cu", "xs_device.cuh"):
+        with open(os.path.join(ROOT, "paper_2105_14782_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def in_cut_triples(lines, nu, W_cut, L):
     c = np.sort(lines.nu_hat)
     lo = np.searchsorted(nu, c - W_cut, side="left")
@@ -364,8 +380,12 @@ def main():
     # launches per step = one per species; triples per launch averaged over species
     avg_triples = triples / len(atm.species)
     achieved = avg_triples * FLOPS_PER_EVAL[kind] / ((k_ms / max(k_n, 1)) / 1000.0) / 1e12
+    traffic = None
+    if (kind == "adj" and len(atm.p_bar) == 100 and kernel_sources_sha256() == TRAFFIC["sources_sha256"]):
+        traffic = TRAFFIC["bytes_per_launch_100_layers"]
     roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": None,
+                "frac": achieved / fp32_peak, "traffic": traffic,
+                "traffic_note": "ncu dram bytes per launch (20-layer capture x 5); null once the kernel changed",
                 "kernel": "linesum_adjoint_kernel<float>" if kind == "adj" else "linesum_kernel<float>",
                 "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
                 "flops_per_eval": FLOPS_PER_EVAL[kind]}

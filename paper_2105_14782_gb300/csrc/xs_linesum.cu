@@ -407,7 +407,7 @@ template <int KIND>
 __device__ __forceinline__ void far_lines(const LineTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                           float2 (&a2)[LS_G / 2], const int (&jg)[LS_G])
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int i = i0; i < i1; ++i) {
         const float4 v0 = tl.q0[i], v1 = tl.q1[i], v3 = tl.q3[i];
         const float2 nb = f2lo(v0), G = f2hi(v0), k0 = f2lo(v1), k1 = f2hi(v1);
@@ -1001,7 +1001,7 @@ template <bool MASKED, bool DEG2 = false>
 __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                               float2 (&aT)[LS_G / 2], float2 (&aB)[LS_G / 2], const int (&jg)[LS_G])
 {
-#pragma unroll 2
+#pragma unroll 4
     for (int i = i0; i < i1; ++i) {
         const float4 v0 = tl.q0[i], t0 = tl.qt0[i], t1 = tl.qt1[i], u0 = tl.qu0[i], u1 = tl.qu1[i];
         const float2 nb = f2lo(v0), G = f2hi(v0);
