@@ -109,72 +109,133 @@ __global__ void tau_adjoint_kernel(SigPtrs sig, GSigPtrs gsig, int S, const doub
     }
 }
 
-__global__ void emission_kernel(const double* __restrict__ dtau, const double* __restrict__ T,
-                                const double* __restrict__ nu, int L, int64_t N, double* __restrict__ F0)
+// Emission solve (Sec. 2.3):  F0 = sum_n Phi_n (1 - T_n) S_n + Phi_L S_B, with
+// Phi_n = prod_{k<n} T_k, T_n = 2 E3(dtau_n), S_n = pi B(nu, T_n), S_B = pi B(nu, T_{L-1}).
+// A block takes 32 grid points (lane = point, coalesced rows of dtau) and its
+// RT_SEG warps take contiguous segments of the layers: each warp reduces its
+// segment to (prod T, local sum), and the segments are chained in order.
+constexpr int RT_SEG = 8;
+
+__device__ __forceinline__ void seg_range(int L, int w, int* n0, int* n1)
 {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= N) return;
-    double v = nu[j];
-    double phi = 1.0, F = 0.0;
-    for (int n = 0; n < L; ++n) {
-        double e2, e3;
-        exp_int23(dtau[(size_t)n * N + j], &e2, &e3);
-        double tr = 2.0 * e3;
-        F += phi * (1.0 - tr) * planck_pi(v, T[n]);
-        phi *= tr;
-    }
-    F0[j] = F + phi * planck_pi(v, T[L - 1]);
+    *n0 = (int)(((int64_t)L * w) / RT_SEG);
+    *n1 = (int)(((int64_t)L * (w + 1)) / RT_SEG);
 }
 
-// Reverse sweep.  With F_n the upward flux leaving layer n (F_L = F_B),
-//   dF0/dT_n = Phi_n (F_{n+1} - S_n),  dF0/dS_n = Phi_n (1 - T_n) (+ Phi_L for n = L-1),
-//   dT_n/d dtau = -2 E2(dtau).
-// Pass 1 (bottom-up) parks F_{n+1} in g_dtau; pass 2 (top-down) overwrites it.
-// The Planck part of dF0/dT_n is reduced per block into part[n][block].
-__global__ void emission_adjoint_kernel(const double* __restrict__ g_F0, const double* __restrict__ dtau,
-                                        const double* __restrict__ T, const double* __restrict__ nu, int L, int64_t N,
-                                        double* __restrict__ g_dtau, double* __restrict__ part)
+__global__ void __launch_bounds__(32 * RT_SEG) emission_kernel(const double* __restrict__ dtau,
+                                                               const double* __restrict__ T,
+                                                               const double* __restrict__ nu, int L, int64_t N,
+                                                               double* __restrict__ F0)
 {
-    __shared__ double red[RT_THREADS];
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    bool valid = j < N;
-    double v = valid ? nu[j] : nu[0];
-    double lam = valid ? g_F0[j] : 0.0;
+    __shared__ double segP[RT_SEG][32], segF[RT_SEG][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = j < N;
+    const double v = valid ? nu[j] : nu[0];
+    int n0, n1;
+    seg_range(L, w, &n0, &n1);
+    double phi = 1.0, F = 0.0;
     if (valid) {
-        double F = planck_pi(v, T[L - 1]);
-        for (int n = L - 1; n >= 0; --n) {
-            size_t i = (size_t)n * N + j;
-            g_dtau[i] = F;
+        for (int n = n0; n < n1; ++n) {
             double e2, e3;
-            exp_int23(dtau[i], &e2, &e3);
-            double tr = 2.0 * e3;
-            F = tr * F + (1.0 - tr) * planck_pi(v, T[n]);
+            exp_int23(dtau[(size_t)n * N + j], &e2, &e3);
+            const double tr = 2.0 * e3;
+            F += phi * (1.0 - tr) * planck_pi(v, T[n]);
+            phi *= tr;
         }
     }
-    double phi = 1.0;
-    for (int n = 0; n < L; ++n) {
-        double gT = 0.0;
-        if (valid) {
-            size_t i = (size_t)n * N + j;
+    segP[w][lane] = phi;
+    segF[w][lane] = F;
+    __syncthreads();
+    if (w == 0 && valid) {
+        double Ft = 0.0, ph = 1.0;
+        for (int s = 0; s < RT_SEG; ++s) {
+            Ft += ph * segF[s][lane];
+            ph *= segP[s][lane];
+        }
+        F0[j] = Ft + ph * planck_pi(v, T[L - 1]);
+    }
+}
+
+// Adjoint of the emission solve for lambda = dlogL/dF0:
+//   dF0/ddtau_n = Phi_n (F_{n+1} - S_n) dT_n/ddtau_n,  dT/ddtau = -2 E2(dtau),
+//   dF0/dS_n = Phi_n (1 - T_n) (+ Phi_L for the bottom source, n = L-1),
+// where F_{n+1} = upward flux below layer n: F_L = S_B, F_n = T_n F_{n+1} + (1 - T_n) S_n.
+// Three passes over each warp's layer segment: (1) T, E2, S stored and the
+// segment's maps F_top = A F_bottom + C and prod T; (2) after chaining the
+// segments, F_{n+1} down the segment; (3) Phi_n along it, g_dtau and the
+// per-layer sums of lambda dF0/dS_n dS_n/dT_n over the block's 32 points.
+__global__ void __launch_bounds__(32 * RT_SEG) emission_adjoint_kernel(
+    const double* __restrict__ g_F0, const double* __restrict__ dtau, const double* __restrict__ T,
+    const double* __restrict__ nu, int L, int64_t N, double* __restrict__ g_dtau, double* __restrict__ part,
+    double* __restrict__ w_tr, double* __restrict__ w_e2, double* __restrict__ w_S)
+{
+    __shared__ double segA[RT_SEG][32], segC[RT_SEG][32], segFin[RT_SEG][32], segPhi[RT_SEG][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    const bool valid = j < N;
+    const double v = valid ? nu[j] : nu[0];
+    const double lam = valid ? g_F0[j] : 0.0;
+    int n0, n1;
+    seg_range(L, w, &n0, &n1);
+    // (1) per-layer factors and the segment's backward map
+    double A = 1.0, Cm = 0.0;
+    if (valid) {
+        for (int n = n1 - 1; n >= n0; --n) {
+            const size_t i = (size_t)n * N + j;
             double e2, e3;
             exp_int23(dtau[i], &e2, &e3);
-            double tr = 2.0 * e3;
-            double B = planck_pi(v, T[n]);
-            double Fn1 = g_dtau[i];
-            g_dtau[i] = lam * phi * (Fn1 - B) * (-2.0 * e2);
+            const double tr = 2.0 * e3, Sn = planck_pi(v, T[n]);
+            w_tr[i] = tr;
+            w_e2[i] = e2;
+            w_S[i] = Sn;
+            Cm = tr * Cm + (1.0 - tr) * Sn;
+            A *= tr;
+        }
+    }
+    segA[w][lane] = A;
+    segC[w][lane] = Cm;
+    __syncthreads();
+    if (w == 0) {
+        // flux entering each segment from below, and Phi at each segment's top
+        double Fb = valid ? planck_pi(v, T[L - 1]) : 0.0;
+        for (int s = RT_SEG - 1; s >= 0; --s) {
+            segFin[s][lane] = Fb;
+            Fb = segA[s][lane] * Fb + segC[s][lane];
+        }
+        double ph = 1.0;
+        for (int s = 0; s < RT_SEG; ++s) {
+            segPhi[s][lane] = ph;
+            ph *= segA[s][lane];
+        }
+    }
+    __syncthreads();
+    // (2) F_{n+1} for each layer of the segment, kept in g_dtau until (3)
+    if (valid) {
+        double F = segFin[w][lane];
+        for (int n = n1 - 1; n >= n0; --n) {
+            const size_t i = (size_t)n * N + j;
+            g_dtau[i] = F;
+            const double tr = w_tr[i];
+            F = tr * F + (1.0 - tr) * w_S[i];
+        }
+    }
+    // (3) forward along the segment
+    double phi = segPhi[w][lane];
+    const double phiL = segPhi[RT_SEG - 1][lane] * segA[RT_SEG - 1][lane];
+    for (int n = n0; n < n1; ++n) {
+        double gT = 0.0;
+        if (valid) {
+            const size_t i = (size_t)n * N + j;
+            const double tr = w_tr[i], Sn = w_S[i];
+            g_dtau[i] = lam * phi * (g_dtau[i] - Sn) * (-2.0 * w_e2[i]);
             double gS = lam * phi * (1.0 - tr);
+            if (n == L - 1) gS += lam * phiL;
             phi *= tr;
-            if (n == L - 1) gS += lam * phi;
-            gT = gS * planck_pi_dT(v, T[n], B);
+            gT = gS * planck_pi_dT(v, T[n], Sn);
         }
-        red[threadIdx.x] = gT;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[(size_t)n * gridDim.x + blockIdx.x] = red[0];
-        __syncthreads();
+        for (int o = 16; o > 0; o >>= 1) gT += __shfl_xor_sync(0xffffffffu, gT, o);
+        if (lane == 0) part[(size_t)n * gridDim.x + blockIdx.x] = gT;
     }
 }
 
@@ -310,22 +371,31 @@ int rt_tau_adjoint(const void* const* sigma, int32_t S, const double* vmr, const
 int rt_emission(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
                 cudaStream_t st)
 {
-    emission_kernel<<<(unsigned)((N + RT_THREADS - 1) / RT_THREADS), RT_THREADS, 0, st>>>(dtau, T, nu, L, N, F0);
+    emission_kernel<<<(unsigned)((N + 31) / 32), 32 * RT_SEG, 0, st>>>(dtau, T, nu, L, N, F0);
     return launched(1);
 }
 
+// [L][nb] per-block layer partials, then T_n, E2_n and S_n as [L][N] each
 size_t rt_emission_ws(int32_t L, int64_t N)
 {
-    int64_t nb = (N + RT_THREADS - 1) / RT_THREADS;
-    return sizeof(double) * (size_t)L * (size_t)nb;
+    int64_t nb = (N + 31) / 32;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    return al(sizeof(double) * (size_t)L * (size_t)nb) + 3 * al(sizeof(double) * (size_t)L * (size_t)N);
 }
 
 int rt_emission_adjoint(const double* g_F0, const double* dtau, const double* T, const double* nu, int32_t L,
                         int64_t N, double* g_dtau, double* g_T, void* ws, cudaStream_t st)
 {
-    int64_t nb = (N + RT_THREADS - 1) / RT_THREADS;
-    double* part = (double*)ws;
-    emission_adjoint_kernel<<<(unsigned)nb, RT_THREADS, 0, st>>>(g_F0, dtau, T, nu, L, N, g_dtau, part);
+    const int64_t nb = (N + 31) / 32;
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    char* base = (char*)ws;
+    double* part = (double*)base;
+    const size_t LN = al(sizeof(double) * (size_t)L * (size_t)N);
+    double* w_tr = (double*)(base + al(sizeof(double) * (size_t)L * (size_t)nb));
+    double* w_e2 = (double*)((char*)w_tr + LN);
+    double* w_S = (double*)((char*)w_e2 + LN);
+    emission_adjoint_kernel<<<(unsigned)nb, 32 * RT_SEG, 0, st>>>(g_F0, dtau, T, nu, L, N, g_dtau, part, w_tr, w_e2,
+                                                                  w_S);
     layer_sum_kernel<<<L, RT_THREADS, 0, st>>>(part, (int)nb, L, g_T);
     return launched(2);
 }
