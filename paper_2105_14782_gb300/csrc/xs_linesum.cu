@@ -7,23 +7,23 @@
 // the rest.  The far part (about 98% of the evaluations) is summed by the main
 // kernels with the Lorentz-wing forms of the asymptotic series (Eq. asywofz) in
 // packed FP32x2 arithmetic; the near part by the near kernels, one thread per
-// grid point, with the full tiered Faddeeva function (xs_device.cuh).  Both use
+// grid point (a polynomial in 1/|z|^2 for |z| >= 6, the series below).  Both use
 // the same integer ranges, so every (line, point) pair is counted exactly once.
 //
 // Main kernels.  Lines are sorted by centre.  A CTA owns one strip of 1,024
 // consecutive grid points of one layer; each of its 4 warps owns 256 points
-// (8 per lane, lane-interleaved) and walks the strip's line window (all lines
-// with an in-cut point in the strip, optionally split into K chunks across CTAs)
+// (8 per lane, lane-interleaved) and walks its own line window (all lines with
+// an in-cut point among its points, optionally split into K parts across CTAs)
 // in 32-line chunks it stages itself in shared memory.  A chunk whose lines all
-// cover the warp's points with no near point runs unmasked (K = 1 form when
-// every pair is at |z| >= 100, else K = 2); other chunks mask per (line, point).
+// cover the warp's points with no near point runs unmasked, with the cheapest
+// wing form its |z| bound allows; other chunks mask per (line, point).
 //
 // Precision (XS_PREC_MIXED): per-line scalars are formed in FP64 and rounded
-// once; line-centre offsets are formed in FP64 relative to the warp's middle
-// grid point and rounded to float (hi + lo where it matters); Voigt values and
-// sums are FP32, with each point's running sum an FP32 (hi, lo) pair updated by
-// TwoSum after every 32 lines.  XS_PREC_FP64 has no fast forms and no near split:
-// every pair goes through the double-precision tiered Faddeeva function.
+// once; line-centre offsets to the warp's middle grid point come from per-line
+// float pairs (hi + lo where it matters); Voigt values and sums are FP32, with
+// each point's running sum an FP32 (hi, lo) pair updated by TwoSum after every
+// 32 lines.  XS_PREC_FP64 has no fast forms and no near split: every pair goes
+// through the double-precision tiered Faddeeva function.
 #include <algorithm>
 #include <type_traits>
 
@@ -282,8 +282,10 @@ __device__ __forceinline__ int64_t lb_jlo(const int2* jr, int64_t n, int v) // f
     return lo;
 }
 
-// Line window of a strip (all lines with an in-cut point in [j0, jlast]) and
-// the kc-th of ksplit equal parts of it, rounded to whole 32-line chunks.
+// Line window of a warp's points (all lines with an in-cut point in [j0, jlast])
+// and the kc-th of ksplit equal parts of it, rounded to whole 32-line chunks.
+// Each warp takes its own window (not the strip's), so no chunk carries lines
+// that miss all of the warp's points.
 // Lane 0 searches, the warp gets the result by shuffle.
 __device__ __forceinline__ void strip_window(const int2* jrange, int64_t nl, int64_t j0, int64_t jlast, int ksplit,
                                              int kc, int64_t* cb, int64_t* ce)
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     WarpPoints<R> pts;
     if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) return;
     int64_t cb, ce;
-    strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
+    strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, kc, &cb, &ce);
     const int layer = layer0 + nloc;
     const float cmin = agg[4 * layer], amin = agg[4 * layer + 1], amax = agg[4 * layer + 2];
     const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
@@ -1127,7 +1129,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     WarpPoints<R> pts;
     if (pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) {
         int64_t cb, ce;
-        strip_window(jrange, nl, j0, jlast, ksplit, kc, &cb, &ce);
+        strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, kc, &cb, &ce);
         const size_t lay = (size_t)nloc * nl;
         const R4* r1g = rec1 + lay;
         const R4* r2g = rec2 + lay;
