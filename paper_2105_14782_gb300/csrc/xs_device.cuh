@@ -295,6 +295,73 @@ __device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float 
     *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
 }
 
+// Per-line table for w_series_tab (near kernels, |z| < 6 so n0 = round(x/h) <= 9):
+// d[n + SER_OFF] = 1/(n^2 h^2 + a^2) for n = 1 .. SER_TAB - 1 - SER_OFF, and 0 for
+// n <= 0 (terms that do not exist).
+constexpr int SER_OFF = 6;  // n0 - 6 >= -6
+constexpr int SER_TAB = 22; // n up to 9 + 6 = 15
+
+__device__ __forceinline__ void series_table(float a, float* d)
+{
+    const float h = Tier<float>::h;
+    const float a2 = a * a;
+#pragma unroll 2
+    for (int i = 0; i < SER_TAB; ++i) {
+        const int n = i - SER_OFF;
+        const float nh = (float)n * h;
+        d[i] = (n >= 1) ? rcp_fast(fmaf(nh, nh, a2)) : 0.0f;
+    }
+}
+
+// The series of w_series_rec with the line's table (series_table) and the
+// terms above and below the peak taken as packed pairs: the same terms at a
+// fraction of the instructions.  0 <= x < 6.3.
+__device__ __forceinline__ void w_series_tab(float xh, float xl, float a, float Kc, const float* dt, float* wr,
+                                             float* wi)
+{
+    const float h = Tier<float>::h;
+    // q^(2k-1), q = exp(-h^2) with h = 0.7f
+    const float Q[6] = {0.61262643f, 0.22992550f, 0.08629359f, 0.03238694f, 0.012155180f, 0.0045619742f};
+    const float x = xh;
+    const int n0 = __float2int_rn(x * (1.0f / h));
+    const float n0h = (float)n0 * h;
+    const float delta = (n0h - xh) - xl;
+    const float E0 = __expf(-delta * delta);
+    const float2 f = make_float2(__expf(-2.0f * h * delta), __expf(2.0f * h * delta));
+    const float R4 = __expf(-4.0f * h * x);
+    const float2 g = make_float2(R4, rcp_fast(R4));
+    const float Rn = __expf(-4.0f * h * x * (float)n0);
+    const float* d0 = dt + (n0 + SER_OFF);
+    // centre term (d0[0] = 0 when n0 = 0)
+    const float ep0 = E0 * Rn;
+    const float dc = d0[0];
+    float2 sc = make_float2(dc * (E0 + ep0), 0.0f);
+    float2 ss = make_float2(n0h * dc * (E0 - ep0), 0.0f);
+    float2 E = make_float2(E0, E0), R = make_float2(Rn, Rn), nh = make_float2(n0h, n0h);
+    const float2 hstep = make_float2(h, -h);
+#pragma unroll
+    for (int k = 1; k <= 6; ++k) {
+        E = __fmul2_rn(__fmul2_rn(E, f), make_float2(Q[k - 1], Q[k - 1])); // (E_{n0+k}, E_{n0-k})
+        R = __fmul2_rn(R, g);
+        nh = __fadd2_rn(nh, hstep);
+        const float2 ep = __fmul2_rn(E, R);
+        const float2 dd = make_float2(d0[k], d0[-k]);
+        sc = __ffma2_rn(dd, __fadd2_rn(E, ep), sc);
+        ss = __ffma2_rn(__fmul2_rn(nh, dd), __fadd2_rn(E, make_float2(-ep.x, -ep.y)), ss);
+    }
+    const float scs = sc.x + sc.y, sss = ss.x + ss.y;
+    const float ex = exp_negsq(xh) * (1.0f - 2.0f * xh * xl);
+    float sax, cax;
+    sincosf(a * x, &sax, &cax);
+    const float c2v = 1.0f - 2.0f * sax * sax; // cos 2ax
+    const float s2 = 2.0f * sax * cax;         // sin 2ax
+    const float sax_a = (a > 0.0f) ? sax * rcp_fast(a) : x;
+    const float s2_a = 2.0f * sax_a * cax;
+    const float hpi = h * (float)(1.0 / PI);
+    *wr = ex * (Kc * c2v + 2.0f * hpi * sax * sax_a) + a * hpi * scs;
+    *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * sss;
+}
+
 template <class R>
 __device__ __forceinline__ void w_small(R x, R xl, R a, R Kc, const R*, R* wr, R* wi)
 {

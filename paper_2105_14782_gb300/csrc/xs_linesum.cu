@@ -683,6 +683,7 @@ struct NearTile {
     float2 xa[32]; // -c bhi, a^2: x to ~1e-7 for the wing polynomial
     int2 jn[32];
     float4 hc[32][4]; // Av C'_0 .. Av C'_12 of the wing polynomial (6 <= |z| < 25)
+    float sd[32][SER_TAB]; // series table (|z| < 6, lines with a < 6)
 };
 
 struct NearAdjTile {
@@ -692,6 +693,7 @@ struct NearAdjTile {
     int2 jn[32];
     float aS[32], nn[32];
     float4 hf[32][4], hg[32][4]; // f_T and f_b wing polynomials (6 <= |z| < 25)
+    float sd[32][SER_TAB];
 };
 
 // |z|^2 from which the near kernels take the wing polynomial in u = 1/|z|^2;
@@ -775,7 +777,7 @@ __device__ __forceinline__ void near_window(const double* nu_hat, int64_t nl, do
 
 // near_sum[n][j] = sum over lines with j in their near range of Av H(x, a),
 // one thread per grid point, lines in ascending order, Neumaier-compensated.
-__global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __restrict__ nu_hat, int64_t nl,
+__global__ void __launch_bounds__(NR_THREADS, 8) near_sum_kernel(const double* __restrict__ nu_hat, int64_t nl,
                                                               const float4* __restrict__ rec2,
                                                               const float* __restrict__ clo,
                                                               const int2* __restrict__ jnear,
@@ -819,6 +821,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
                 float C[ASY_N];
                 asy_coeffs(p2.y, p2.z, C);
                 store16(tl.hc[lane], C, ASY_N);
+                if (p2.y * p2.y < NEAR_POLY_Z2) series_table(p2.y, tl.sd[lane]);
             }
         } else {
             tl.jn[lane] = make_int2(1, 0);
@@ -841,7 +844,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
                     float x, xl;
                     scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
                     float wr, wi;
-                    w_small<float>(x, xl, p2.y, p2.w, nullptr, &wr, &wi);
+                    w_series_tab(x, xl, p2.y, p2.w, tl.sd[i], &wr, &wi);
                     acc = fmaf(p2.z, wr, acc);
                 }
             }
@@ -857,7 +860,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_sum_kernel(const double* __re
 
 // The adjoint's near pairs: per point, sum of lambda_j (f_T, f_b) (see
 // linesum_adjoint_kernel), reduced per block into part[layer][block].
-__global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
+__global__ void __launch_bounds__(NR_THREADS, 6) near_adjoint_kernel(
     const double* __restrict__ nu_hat, int64_t nl, const float4* __restrict__ rec2, const float* __restrict__ clo,
     const float* __restrict__ rec3, const int2* __restrict__ jnear, const float* __restrict__ agg,
     const double* __restrict__ nu, int64_t N, int layer0, const double* __restrict__ T,
@@ -907,6 +910,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
                     asy_coeffs_adj(p2.y, p2.z, aS, half_invT, nn, F, G);
                     store16(tl.hf[lane], F, ASY_N + 1);
                     store16(tl.hg[lane], G, ASY_N + 1);
+                    if (p2.y * p2.y < NEAR_POLY_Z2) series_table(p2.y, tl.sd[lane]);
                 }
             } else {
                 tl.jn[lane] = make_int2(1, 0);
@@ -930,7 +934,7 @@ __global__ void __launch_bounds__(NR_THREADS) near_adjoint_kernel(
                         scaled_pair(ohi - tl.bhi[i], olo - tl.blo[i], p2.x, tl.clo[i], &x, &xl);
                         const float a = p2.y;
                         float wr, wi;
-                        w_small<float>(x, xl, a, p2.w, nullptr, &wr, &wi);
+                        w_series_tab(x, xl, a, p2.w, tl.sd[i], &wr, &wi);
                         // w' = -2 z w + 2i/sqrt(pi);  H_x = Re w', H_a = -Im w'
                         const float dr = -2.0f * (x * wr - a * wi);
                         const float di = -2.0f * (x * wi + a * wr) + (float)(2.0 * INV_SQRTPI);
