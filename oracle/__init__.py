@@ -214,3 +214,101 @@ def logl_grad(atm, theta, dobs, sig_obs):
                                _p(qexp), nu.size, _p(nu), P.size, _p(P), _p(dP), atm.gravity, atm.mu,
                                atm.kappa_coef, atm.wing_cut, _p(th), _p(d), _p(s), _p(grad), _p(F0))
     return ll, grad, F0
+
+
+# ------------------------------------------------------------------ MODIT (Sec. 2.1.2)
+
+
+def modit_fft_length(nu_min, nu_max, N, nu_hat):
+    """Smallest power of two M >= 2 (N + farthest centre outside the grid, in
+    steps of q = R0 ln nu) + 4: the padded period of the q axis, long enough that
+    every line's profile, cut at half a period, covers the whole grid."""
+    R0 = (N - 1) / np.log(nu_max / nu_min)
+    q = R0 * np.log(np.asarray(nu_hat, dtype=np.float64) / nu_min)
+    out = max(0.0, -float(q.min()), float(q.max()) - (N - 1)) if q.size else 0.0
+    need = 2 * (N + int(np.ceil(out))) + 4
+    return 1 << int(np.ceil(np.log2(need)))
+
+
+def modit_gamma_grid(gq, n_gamma):
+    """n_gamma nodes log-spaced from min to max of the normalised widths gq."""
+    lo, hi = np.log(gq.min()), np.log(gq.max())
+    if n_gamma < 2 or hi <= lo:
+        return np.array([np.exp(lo)] * max(n_gamma, 1))
+    return np.exp(lo + (hi - lo) * np.arange(n_gamma) / (n_gamma - 1))
+
+
+def modit_lsd(lines, nu_min, nu_max, N, T, P_bar, sb, n_gamma, n_fft):
+    """Lineshape distribution matrix S_jk of one layer (Sec. 2.1.2): each line
+    adds its strength S(T) to the two q nodes around q_l = R0 ln(nu_hat/nu_min)
+    and the two log-spaced gamma' nodes around gamma'_l = R0 gamma/nu_hat, with
+    weights linear in q and in ln gamma'.  Node q = j is stored at j mod n_fft.
+    Returns (lsd [n_gamma][n_fft], gamma' nodes, beta' = R0 beta/nu_hat, R0)."""
+    nu_hat = np.asarray(lines.nu_hat, dtype=np.float64)
+    R0 = (N - 1) / np.log(nu_max / nu_min)
+    S, beta, gam = line_params(lines, T, P_bar, sb)
+    q = R0 * np.log(nu_hat / nu_min)
+    gq = R0 * gam / nu_hat
+    nodes = modit_gamma_grid(gq, n_gamma)
+    lsd = np.zeros((n_gamma, n_fft))
+    j0 = np.floor(q).astype(np.int64)
+    wq = q - j0
+    if n_gamma >= 2 and nodes[-1] > nodes[0]:
+        t = (np.log(gq) - np.log(nodes[0])) / (np.log(nodes[-1]) - np.log(nodes[0])) * (n_gamma - 1)
+        k0 = np.clip(np.floor(t).astype(np.int64), 0, n_gamma - 2)
+        wk = t - k0
+    else:
+        k0 = np.zeros(q.size, dtype=np.int64)
+        wk = np.zeros(q.size)
+    for dj, fj in ((0, 1.0 - wq), (1, wq)):
+        for dk, fk in ((0, 1.0 - wk), (1, wk)):
+            kk = np.minimum(k0 + dk, n_gamma - 1)
+            np.add.at(lsd, (kk, (j0 + dj) % n_fft), S * fj * fk)
+    beta_q = float(np.mean(R0 * beta / nu_hat)) if nu_hat.size else 0.0
+    return lsd, nodes, beta_q, R0
+
+
+def modit_image_sum(M):
+    """A(d) = sum over p != 0 of 1/(pi (d + pM)^2) on the period d = -M/2 .. M/2-1
+    (index d mod M), from sum_p 1/(d + pM)^2 = (pi/M)^2 / sin^2(pi d/M); near d = 0
+    from the Laurent series of csc^2 to avoid cancellation."""
+    d = np.arange(M, dtype=np.float64)
+    d = np.where(d < M / 2, d, d - M)
+    x = np.pi * d / M
+    out = np.empty(M)
+    small = np.abs(x) < 0.3
+    xs = x[small]
+    out[small] = (np.pi / M ** 2) * (1.0 / 3 + xs ** 2 / 15 + 2 * xs ** 4 / 189 + xs ** 6 / 675
+                                     + 2 * xs ** 8 / 10395)
+    xl, dl = x[~small], d[~small]
+    out[~small] = ((np.pi / M) ** 2 / np.sin(xl) ** 2 - 1.0 / dl ** 2) / np.pi
+    return out
+
+
+def modit(lines, nu_min, nu_max, N, T, P_bar, sb=1.0, n_gamma=16, n_fft=None):
+    """sigma[L][N] on the log grid nu_i = nu_min (nu_max/nu_min)^(i/(N-1)) by
+    Eq. MODIT: sigma(q_i) = sum_k IDFT[ DFT(S_.k) K_k(f) ], f the DFT frequency in
+    cycles per q step, then sigma(nu) = sigma(q) R0/nu.  K_k is the Voigt
+    transform exp(-2 pi^2 beta'^2 f^2 - 2 pi gamma'_k |f|) with the Lorentz
+    aliasing removed (reading): the periodic images of each Lorentz profile,
+    gamma'_k A(d) to first order in gamma'/M, are subtracted in the transform,
+    K_k = exp(-2 pi^2 beta'^2 f^2) (exp(-2 pi gamma'_k |f|) - gamma'_k DFT(A)(f)).
+    The result is the linear convolution with each profile cut at half the
+    padded period, beyond the grid; there is no other wing cut."""
+    T = np.atleast_1d(np.asarray(T, dtype=np.float64))
+    P = np.atleast_1d(np.asarray(P_bar, dtype=np.float64))
+    if n_fft is None:
+        n_fft = modit_fft_length(nu_min, nu_max, N, lines.nu_hat)
+    nu = nu_min * (nu_max / nu_min) ** (np.arange(N) / (N - 1))
+    f = np.arange(n_fft // 2 + 1) / n_fft
+    Ahat = np.fft.rfft(modit_image_sum(n_fft)).real
+    out = np.empty((T.size, N))
+    for n in range(T.size):
+        lsd, nodes, bq, R0 = modit_lsd(lines, nu_min, nu_max, N, T[n], P[n], sb, n_gamma, n_fft)
+        gauss = np.exp(-2.0 * np.pi ** 2 * bq ** 2 * f ** 2)
+        Y = np.zeros(f.size, dtype=np.complex128)
+        for k in range(n_gamma):
+            Y += np.fft.rfft(lsd[k]) * gauss * (np.exp(-2.0 * np.pi * nodes[k] * f) - nodes[k] * Ahat)
+        y = np.fft.irfft(Y, n=n_fft)
+        out[n] = y[:N] * R0 / nu
+    return out
