@@ -247,6 +247,37 @@ int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, 
                        size_t workspace_bytes, xs_stream stream);
 
 /*
+ * MODIT (Sec. 2.1.2, Eqs. FTFT, ftmodit, MODIT): the cross-section of one species
+ * on the log grid nu_i = nu_min (nu_max/nu_min)^(i/(N-1)), i = 0..N-1, from a
+ * lineshape distribution and FFT convolution instead of a line-by-line sum.
+ * With R0 = (N-1)/ln(nu_max/nu_min) and q = R0 ln(nu/nu_min) (unit steps):
+ *   - each line adds S(T) (Eq. Slog) to the two q nodes around its centre and the
+ *     two of n_gamma log-spaced nodes (per layer, from the smallest to the largest
+ *     gamma' = R0 gamma/nu_hat) around its width, with weights linear in q and in
+ *     ln gamma';
+ *   - sigma(q) = sum_k IFFT[ FFT(S_k) exp(-2 pi^2 beta'^2 f^2) (exp(-2 pi gamma'_k f)
+ *     - gamma'_k FFT(A)) ], beta' = R0 beta/nu_hat, and sigma(nu) = sigma(q) R0/nu.
+ *     A is the sum of a unit-width Lorentzian's periodic images on the padded q
+ *     axis; subtracting it removes the Lorentz aliasing to first order in
+ *     gamma'/n_fft (the paper names an aliasing correction without stating it).
+ * No wing cut: each profile reaches half the period n_fft on either side.  n_fft
+ * (a power of two, >= N + 2) is the padded period; for profiles that cover the
+ * whole grid use n_fft >= 2 (N + m), m the farthest centre outside the grid in q
+ * steps.  n_gamma 1..32.  Lines sorted by centre (as for xs_compute), device
+ * arrays; T, P_bar [L] device; sigma [L][N] device, double (XS_PREC_FP64:
+ * FP64 distribution and FFT) or float (XS_PREC_MIXED: FP32 distribution and
+ * FFT, strengths scaled by 2^80 inside).  The distribution is summed in a fixed
+ * order; the FFTs are cuFFT's (one plan per length and batch, created on first
+ * use without a work area of its own).  Errors: XS_EINVAL for bad arguments or a
+ * workspace below modit_workspace_bytes; XS_ETOOBIG if cuFFT asks for more work
+ * area than the workspace reserves; XS_ECUDA on launch or cuFFT failure.
+ */
+size_t modit_workspace_bytes(int32_t L, int32_t n_gamma, int64_t n_fft, int prec);
+int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N, const double* T,
+                  const double* P_bar, int32_t L, double broad_scale, int32_t n_gamma, int64_t n_fft, int prec,
+                  void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream);
+
+/*
  * Diagnostics (no paper counterpart).  xs_profile(1) makes the library record a
  * CUDA event pair around every line-sum kernel launch (forward and adjoint,
  * on the launching stream) until xs_profile(0); xs_profile_read synchronises

@@ -11,7 +11,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxs.so")
-SOURCES = ["xs_linesum.cu", "xs_rt.cu", "xs_api.cu", "xs_noalloc.cu"]
+SOURCES = ["xs_linesum.cu", "xs_rt.cu", "xs_api.cu", "xs_noalloc.cu", "xs_modit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -58,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         for _, err in results:
             sys.stderr.write(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcudart"]
+    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in results] + ["-lcufft", "-lcudart"]
     p = subprocess.run(cmd, capture_output=True, text=True)
     if p.returncode != 0:
         raise RuntimeError(f"link failed:\n{p.stderr}")

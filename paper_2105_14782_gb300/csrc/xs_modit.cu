@@ -1,0 +1,390 @@
+// MODIT (Sec. 2.1.2, Eq. MODIT): the cross-section of many lines through a
+// lineshape distribution on the log grid and FFT convolution.
+//
+// Grid: nu_i = nu_min exp(i/R0), i = 0..N-1, R0 = (N-1)/ln(nu_max/nu_min), so the
+// variable q = R0 ln(nu/nu_min) steps by 1.  For each layer:
+//   1. every line's S(T) (Eq. Slog) and normalised width gamma' = R0 gamma/nu_hat;
+//      per layer the min and max of gamma' (modit_range_kernel);
+//   2. the lineshape distribution S[k][j]: each line adds S to the two q nodes
+//      around q_l = R0 ln(nu_hat/nu_min) and the two ln gamma' nodes around its
+//      width, with linear weights (modit_lsd_kernel).  One thread per q node
+//      gathers the lines in [j-1, j+1) by binary search on the sorted centres, so
+//      the sum has a fixed order (no atomics);
+//   3. batched real FFTs of the n_gamma rows (cuFFT);
+//   4. Y[f] = sum_k FT(S_k)[f] K_k[f], K_k = exp(-2 pi^2 beta'^2 f^2)
+//      (exp(-2 pi gamma'_k |f|) - gamma'_k DFT(A)[f]), beta' = R0 beta/nu_hat (common
+//      to all lines of a species at one T), A the sum of a unit Lorentzian's periodic
+//      images (its first-order aliasing, removed here);
+//   5. inverse FFT per layer, then sigma(nu_i) = sigma(q_i) R0/nu_i.
+// The q axis is periodic with the caller's length n_fft (a power of two); node j
+// lives at slot j mod n_fft, nodes -(n_fft-N)/2 .. (n_fft+N)/2 - 1 are gathered.
+#include <cufft.h>
+
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <type_traits>
+
+#include "xs_device.cuh"
+#include "xs_internal.h"
+
+namespace xsd {
+
+constexpr int MODIT_MAX_GAMMA = 32;
+constexpr int MODIT_THREADS = 256;
+
+template <class R> struct CplxOf;
+template <> struct CplxOf<double> { using type = cufftDoubleComplex; };
+template <> struct CplxOf<float> { using type = cufftComplex; };
+
+// S(T) (Eq. Slog, scaled) and gamma (Eq. gammahitran, reduced) of one line.
+__device__ __forceinline__ void modit_line(const double* __restrict__ nu_hat, const double* __restrict__ ln_S0,
+                                           const double* __restrict__ elower, const double* __restrict__ gamma_ref,
+                                           const double* __restrict__ n_temp, int64_t l, double qexp, double Tn,
+                                           double Pn, double sb, double scale, double* S, double* gam)
+{
+    const double nuh = nu_hat[l];
+    const double lnTr = log(Tn / Tref);
+    const double boltz = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref) - qexp * lnTr);
+    const double stim = expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref);
+    *S = boltz * stim * scale;
+    *gam = sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (Pn / bar_per_atm);
+}
+
+__global__ void modit_range_init_kernel(unsigned long long* range, int L)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < L) {
+        range[2 * i] = 0x7ff0000000000000ull; // +inf
+        range[2 * i + 1] = 0ull;
+    }
+}
+
+// per layer min and max of gamma' = R0 gamma/nu_hat (positive doubles order like
+// their bit patterns)
+__global__ void modit_range_kernel(const double* __restrict__ nu_hat, const double* __restrict__ gamma_ref,
+                                   const double* __restrict__ n_temp, int64_t nl, const double* __restrict__ T,
+                                   const double* __restrict__ P, double sb, double R0,
+                                   unsigned long long* __restrict__ range)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    double gmin = __longlong_as_double(0x7ff0000000000000ll), gmax = 0.0;
+    if (l < nl) {
+        const double lnTr = log(T[n] / Tref);
+        const double g = R0 * sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (P[n] / bar_per_atm) / nu_hat[l];
+        gmin = g;
+        gmax = g;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        gmin = fmin(gmin, __shfl_xor_sync(0xffffffffu, gmin, o));
+        gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    }
+    if ((threadIdx.x & 31) == 0 && gmax > 0.0) {
+        atomicMin(&range[2 * n], (unsigned long long)__double_as_longlong(gmin));
+        atomicMax(&range[2 * n + 1], (unsigned long long)__double_as_longlong(gmax));
+    }
+}
+
+__device__ __forceinline__ int64_t first_at_least(const double* v, int64_t n, double x) // first i with v[i] >= x
+{
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t m = (lo + hi) >> 1;
+        if (v[m] >= x) hi = m; else lo = m + 1;
+    }
+    return lo;
+}
+
+// One thread per (layer, slot): node j = slot, or slot - M for the left padding.
+// Lines with floor(q_l) == j give weight 1 - w, those with floor(q_l) == j - 1
+// give w (w = q_l - floor(q_l)); the candidates come from a binary search with a
+// half-node margin, the decision from each line's own q_l.
+template <class R>
+__global__ void __launch_bounds__(MODIT_THREADS) modit_lsd_kernel(
+    const double* __restrict__ nu_hat, const double* __restrict__ ln_S0, const double* __restrict__ elower,
+    const double* __restrict__ gamma_ref, const double* __restrict__ n_temp, int64_t nl, double qexp,
+    const double* __restrict__ T, const double* __restrict__ P, double sb, double scale, double nu_min, double R0,
+    int64_t N, int64_t M, int ng, const unsigned long long* __restrict__ range, R* __restrict__ lsd)
+{
+    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (s >= M) return;
+    const int64_t j = (s < (M + N) / 2) ? s : s - M;
+    const double Tn = T[n], Pn = P[n];
+    const double gmin = __longlong_as_double((long long)range[2 * n]);
+    const double gmax = __longlong_as_double((long long)range[2 * n + 1]);
+    const double lg0 = log(gmin);
+    const double dlg = (ng >= 2 && gmax > gmin) ? (log(gmax) - lg0) / (double)(ng - 1) : 0.0;
+    double acc[MODIT_MAX_GAMMA];
+#pragma unroll
+    for (int k = 0; k < MODIT_MAX_GAMMA; ++k) acc[k] = 0.0;
+    const int64_t b = first_at_least(nu_hat, nl, nu_min * exp(((double)j - 1.5) / R0));
+    const int64_t e = first_at_least(nu_hat, nl, nu_min * exp(((double)j + 1.5) / R0));
+    for (int64_t l = b; l < e; ++l) {
+        const double q = R0 * log(nu_hat[l] / nu_min);
+        const double fq = floor(q);
+        double wq;
+        if (fq == (double)j) wq = 1.0 - (q - fq);
+        else if (fq == (double)(j - 1)) wq = q - fq;
+        else continue;
+        double S, gam;
+        modit_line(nu_hat, ln_S0, elower, gamma_ref, n_temp, l, qexp, Tn, Pn, sb, scale, &S, &gam);
+        const double g = R0 * gam / nu_hat[l];
+        int k0 = 0;
+        double wk = 0.0;
+        if (dlg > 0.0) {
+            const double t = (log(g) - lg0) / dlg;
+            k0 = min(max((int)floor(t), 0), ng - 2);
+            wk = t - (double)k0;
+        }
+        const double v = S * wq;
+#pragma unroll
+        for (int k = 0; k < MODIT_MAX_GAMMA; ++k) {
+            if (k == k0) acc[k] += v * (1.0 - wk);
+            if (k == k0 + 1) acc[k] += v * wk;
+        }
+    }
+    for (int k = 0; k < ng; ++k) lsd[((size_t)n * ng + k) * M + s] = (R)acc[k];
+}
+
+// A(d) = sum over p != 0 of 1/(pi (d + pM)^2) on one period (index d mod M):
+// (pi/M)^2/sin^2(pi d/M) - 1/d^2 over pi, near d = 0 from the Laurent series of csc^2.
+template <class R>
+__global__ void modit_images_kernel(int64_t M, R* __restrict__ A)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    const double d = (i < M / 2) ? (double)i : (double)(i - M);
+    const double x = PI * d / (double)M;
+    double v;
+    if (fabs(x) < 0.3) {
+        const double x2 = x * x;
+        v = (PI / ((double)M * (double)M)) *
+            (1.0 / 3 + x2 * (1.0 / 15 + x2 * (2.0 / 189 + x2 * (1.0 / 675 + x2 * (2.0 / 10395)))));
+    } else {
+        const double sx = sin(x);
+        v = ((PI / M) * (PI / M) / (sx * sx) - 1.0 / (d * d)) / PI;
+    }
+    A[i] = (R)v;
+}
+
+// Y[n][m] = sum_k Z[n][k][m] K_k(m) for m = 0..M/2
+template <class R>
+__global__ void modit_multiply_kernel(const typename CplxOf<R>::type* __restrict__ Z,
+                                      const typename CplxOf<R>::type* __restrict__ Ahat, int64_t M, int ng,
+                                      const double* __restrict__ T, double mass, double R0,
+                                      const unsigned long long* __restrict__ range,
+                                      typename CplxOf<R>::type* __restrict__ Y)
+{
+    const int64_t m = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    const int64_t H = M / 2 + 1;
+    if (m >= H) return;
+    const double gmin = __longlong_as_double((long long)range[2 * n]);
+    const double gmax = __longlong_as_double((long long)range[2 * n + 1]);
+    const double lg0 = log(gmin);
+    const double dlg = (ng >= 2 && gmax > gmin) ? (log(gmax) - lg0) / (double)(ng - 1) : 0.0;
+    const double bq = sqrt(kB * T[n] / (mass * amu)) * R0 / cL; // beta' (q units)
+    const double f = (double)m / (double)M;
+    const double gauss = exp(-2.0 * PI * PI * bq * bq * f * f);
+    const double ah = (double)Ahat[m].x;
+    double yr = 0.0, yi = 0.0;
+    for (int k = 0; k < ng; ++k) {
+        const double g = exp(lg0 + dlg * (double)k);
+        const double K = gauss * (exp(-2.0 * PI * g * f) - g * ah);
+        const typename CplxOf<R>::type z = Z[((size_t)n * ng + k) * H + m];
+        yr += (double)z.x * K;
+        yi += (double)z.y * K;
+    }
+    Y[(size_t)n * H + m].x = (R)yr;
+    Y[(size_t)n * H + m].y = (R)yi;
+}
+
+template <class R>
+__global__ void modit_finish_kernel(const R* __restrict__ y, int64_t M, int64_t N, int L, double R0, double nu_min,
+                                    double unscale, void* __restrict__ sigma)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = blockIdx.y;
+    if (i >= N) return;
+    const double nu = nu_min * exp((double)i / R0);
+    const double v = (double)y[(size_t)n * M + i] / (double)M * R0 / nu * unscale;
+    if (std::is_same<R, float>::value) ((float*)sigma)[(size_t)n * N + i] = (float)v;
+    else ((double*)sigma)[(size_t)n * N + i] = v;
+}
+
+} // namespace xsd
+
+namespace {
+
+using namespace xsd;
+
+size_t al256(size_t b) { return (b + 255) / 256 * 256; }
+
+struct ModitPlan {
+    size_t range, lsd, Z, A, Ahat, Y, work, total, work_bytes;
+};
+
+ModitPlan modit_plan(int32_t L, int32_t ng, int64_t M, int prec)
+{
+    const size_t rs = (prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
+    const size_t H = (size_t)M / 2 + 1;
+    ModitPlan p{};
+    size_t off = 0;
+    auto take = [&](size_t b) {
+        size_t o = off;
+        off += al256(b);
+        return o;
+    };
+    p.range = take(2 * sizeof(unsigned long long) * (size_t)L);
+    p.lsd = take(rs * (size_t)L * ng * M); // reused for the inverse transforms' output
+    p.Z = take(2 * rs * (size_t)L * ng * H);
+    p.A = take(rs * (size_t)M);
+    p.Ahat = take(2 * rs * H);
+    p.Y = take(2 * rs * (size_t)L * H);
+    // cuFFT work area: reserved at the size of the largest complex array
+    p.work_bytes = std::max<size_t>((size_t)16 << 20, 2 * rs * (size_t)L * ng * H);
+    p.work = take(p.work_bytes);
+    p.total = off;
+    return p;
+}
+
+// cuFFT plans, created once per (device, length, batch, type) without their own
+// work area (the caller's workspace provides it).
+std::mutex g_fft_mu;
+std::map<std::tuple<int, int64_t, int64_t, int>, std::pair<cufftHandle, size_t>> g_fft_plans;
+
+int fft_plan(int64_t M, int64_t batch, cufftType type, cufftHandle* out, size_t* work)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return XS_ECUDA;
+    auto key = std::make_tuple(dev, M, batch, (int)type);
+    auto it = g_fft_plans.find(key);
+    if (it != g_fft_plans.end()) {
+        *out = it->second.first;
+        *work = it->second.second;
+        return XS_OK;
+    }
+    cufftHandle h;
+    if (cufftCreate(&h) != CUFFT_SUCCESS) return XS_ECUDA;
+    if (cufftSetAutoAllocation(h, 0) != CUFFT_SUCCESS) return XS_ECUDA;
+    long long n = M;
+    size_t ws = 0;
+    const bool fwd = (type == CUFFT_D2Z || type == CUFFT_R2C);
+    long long idist = fwd ? M : M / 2 + 1, odist = fwd ? M / 2 + 1 : M;
+    if (cufftMakePlanMany64(h, 1, &n, nullptr, 1, idist, nullptr, 1, odist, type, batch, &ws) != CUFFT_SUCCESS) {
+        cufftDestroy(h);
+        return XS_ECUDA;
+    }
+    g_fft_plans[key] = {h, ws};
+    *out = h;
+    *work = ws;
+    return XS_OK;
+}
+
+template <class R>
+int fft_exec(int64_t M, int64_t batch, bool forward, void* in, void* out, void* work, size_t work_bytes,
+             cudaStream_t st)
+{
+    constexpr bool D = std::is_same<R, double>::value;
+    const cufftType type = forward ? (D ? CUFFT_D2Z : CUFFT_R2C) : (D ? CUFFT_Z2D : CUFFT_C2R);
+    std::lock_guard<std::mutex> lk(g_fft_mu);
+    cufftHandle h;
+    size_t ws = 0;
+    int r = fft_plan(M, batch, type, &h, &ws);
+    if (r != XS_OK) return r;
+    if (ws > work_bytes) return XS_ETOOBIG;
+    if (cufftSetStream(h, st) != CUFFT_SUCCESS || cufftSetWorkArea(h, work) != CUFFT_SUCCESS) return XS_ECUDA;
+    cufftResult e;
+    if (D) {
+        e = forward ? cufftExecD2Z(h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out)
+                    : cufftExecZ2D(h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
+    } else {
+        e = forward ? cufftExecR2C(h, (cufftReal*)in, (cufftComplex*)out)
+                    : cufftExecC2R(h, (cufftComplex*)in, (cufftReal*)out);
+    }
+    xsi::count_launch();
+    return e == CUFFT_SUCCESS ? XS_OK : XS_ECUDA;
+}
+
+template <class R>
+int run_modit(const xs_lines* ln, double nu_min, double nu_max, int64_t N, const double* T, const double* P,
+              int32_t L, double sb, int32_t ng, int64_t M, void* sigma, char* ws, const ModitPlan& p,
+              cudaStream_t st)
+{
+    using C = typename CplxOf<R>::type;
+    constexpr bool FAST = std::is_same<R, float>::value;
+    const double R0 = (double)(N - 1) / log(nu_max / nu_min);
+    const double scale = FAST ? MIXED_SCALE : 1.0, unscale = FAST ? MIXED_UNSCALE : 1.0;
+    const int64_t nl = ln->n;
+    const int64_t H = M / 2 + 1;
+    auto* range = (unsigned long long*)(ws + p.range);
+    R* lsd = (R*)(ws + p.lsd);
+    C* Z = (C*)(ws + p.Z);
+    R* A = (R*)(ws + p.A);
+    C* Ahat = (C*)(ws + p.Ahat);
+    C* Y = (C*)(ws + p.Y);
+    void* work = ws + p.work;
+    if (nl == 0) {
+        const size_t es = FAST ? sizeof(float) : sizeof(double);
+        return cudaMemsetAsync(sigma, 0, es * (size_t)L * N, st) == cudaSuccess ? XS_OK : XS_ECUDA;
+    }
+    modit_range_init_kernel<<<(L + 255) / 256, 256, 0, st>>>(range, L);
+    modit_range_kernel<<<dim3((unsigned)((nl + 255) / 256), (unsigned)L), 256, 0, st>>>(
+        ln->nu_hat, ln->gamma_ref, ln->n_temp, nl, T, P, sb, R0, range);
+    modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 1) / MODIT_THREADS), (unsigned)L), MODIT_THREADS, 0,
+                          st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp, nl, ln->q_exponent,
+                                T, P, sb, scale, nu_min, R0, N, M, ng, range, lsd);
+    modit_images_kernel<R><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, A);
+    xsi::count_launch(4);
+    if (cudaGetLastError() != cudaSuccess) return XS_ECUDA;
+    int r = fft_exec<R>(M, (int64_t)L * ng, true, lsd, Z, work, p.work_bytes, st);
+    if (r != XS_OK) return r;
+    r = fft_exec<R>(M, 1, true, A, Ahat, work, p.work_bytes, st);
+    if (r != XS_OK) return r;
+    modit_multiply_kernel<R><<<dim3((unsigned)((H + 255) / 256), (unsigned)L), 256, 0, st>>>(
+        Z, Ahat, M, ng, T, ln->mass_amu, R0, range, Y);
+    xsi::count_launch();
+    r = fft_exec<R>(M, L, false, Y, lsd, work, p.work_bytes, st); // y reuses the distribution's memory
+    if (r != XS_OK) return r;
+    modit_finish_kernel<R><<<dim3((unsigned)((N + 255) / 256), (unsigned)L), 256, 0, st>>>(lsd, M, N, L, R0,
+                                                                                         nu_min, unscale, sigma);
+    xsi::count_launch();
+    return cudaGetLastError() == cudaSuccess ? XS_OK : XS_ECUDA;
+}
+
+bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+
+} // namespace
+
+extern "C" {
+
+size_t modit_workspace_bytes(int32_t L, int32_t n_gamma, int64_t n_fft, int prec)
+{
+    if (L <= 0 || n_gamma < 1 || n_gamma > MODIT_MAX_GAMMA || !pow2(n_fft)) return 0;
+    if (prec != XS_PREC_FP64 && prec != XS_PREC_MIXED) return 0;
+    return modit_plan(L, n_gamma, n_fft, prec).total;
+}
+
+int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N, const double* T,
+                  const double* P_bar, int32_t L, double broad_scale, int32_t n_gamma, int64_t n_fft, int prec,
+                  void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream)
+{
+    if (!lines || lines->n < 0 || !T || !P_bar || !sigma || !workspace || L <= 0 || N < 2) return XS_EINVAL;
+    if (lines->n > 0 && (!lines->nu_hat || !lines->ln_S0 || !lines->elower || !lines->gamma_ref || !lines->n_temp))
+        return XS_EINVAL;
+    if (!(nu_min > 0.0) || !(nu_max > nu_min) || !(broad_scale > 0.0) || !(lines->mass_amu > 0.0)) return XS_EINVAL;
+    if (n_gamma < 1 || n_gamma > MODIT_MAX_GAMMA || !pow2(n_fft) || n_fft < N + 2) return XS_EINVAL;
+    if (prec != XS_PREC_FP64 && prec != XS_PREC_MIXED) return XS_EINVAL;
+    const ModitPlan p = modit_plan(L, n_gamma, n_fft, prec);
+    if (workspace_bytes < p.total) return XS_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (prec == XS_PREC_FP64)
+        return run_modit<double>(lines, nu_min, nu_max, N, T, P_bar, L, broad_scale, n_gamma, n_fft, sigma,
+                                 (char*)workspace, p, st);
+    return run_modit<float>(lines, nu_min, nu_max, N, T, P_bar, L, broad_scale, n_gamma, n_fft, sigma,
+                            (char*)workspace, p, st);
+}
+
+} // extern "C"

@@ -80,6 +80,9 @@ def lib():
         L.xs_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
         L.xs_launch_count.restype = C.c_uint64
+        L.modit_workspace_bytes.restype = sz
+        L.modit_workspace_bytes.argtypes = [i32, i32, i64, i]
+        L.modit_compute.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, sz, vp]
         _lib = L
     return _lib
 
@@ -158,6 +161,37 @@ def xs_compute_adjoint(lines: DeviceLines, nu, T, P_bar, g_sigma, broad_scale=1.
         C.byref(s), _dev(nu), N, _dev(T), _dev(P_bar), L, float(broad_scale), float(wing_cut), prec, _dev(g_sigma),
         _dev(g_T), _dev(g_b), _dev(workspace), workspace.numel(), _stream(stream)))
     return g_T, g_b
+
+
+def modit_fft_length(nu_min, nu_max, N, lines: "DeviceLines"):
+    """Smallest power of two >= 2 (N + farthest centre outside the grid, in q
+    steps) + 4, so that every profile covers the whole grid."""
+    R0 = (N - 1) / math.log(nu_max / nu_min)
+    if lines.n:
+        lo, hi = float(lines.nu_hat[0].item()), float(lines.nu_hat[-1].item())
+        out = max(0.0, -R0 * math.log(lo / nu_min), R0 * math.log(hi / nu_min) - (N - 1))
+    else:
+        out = 0.0
+    need = 2 * (N + int(math.ceil(out))) + 4
+    return 1 << int(math.ceil(math.log2(need)))
+
+
+def modit_compute(lines: DeviceLines, nu_min, nu_max, N, T, P_bar, broad_scale=1.0, n_gamma=16, n_fft=None,
+                  prec=PREC_FP64, out=None, workspace=None, stream=None):
+    """MODIT cross-section sigma[L][N] on the log grid nu_min .. nu_max (N points)."""
+    L = T.numel()
+    if n_fft is None:
+        n_fft = modit_fft_length(nu_min, nu_max, N, lines)
+    dt = torch.float32 if prec == PREC_MIXED else torch.float64
+    if out is None:
+        out = torch.empty((L, N), dtype=dt, device=T.device)
+    if workspace is None:
+        workspace = _ws(lib().modit_workspace_bytes(L, n_gamma, n_fft, prec), T.device)
+    s = lines.struct()
+    _check("modit_compute", lib().modit_compute(C.byref(s), float(nu_min), float(nu_max), N, _dev(T), _dev(P_bar), L,
+                                                float(broad_scale), n_gamma, n_fft, prec, _dev(out),
+                                                _dev(workspace), workspace.numel(), _stream(stream)))
+    return out
 
 
 def _ptrs(ts):

@@ -1,0 +1,86 @@
+"""MODIT on the GPU (modit_compute) against the oracle's MODIT (Sec. 2.1.2,
+Eq. MODIT) on the same seeded lines: FP64 to 1e-10 of each layer's maximum
+(FFT rounding), FP32 to 1e-5 of it, at a small size with lines beyond the grid
+edges and at the size of the 220,000-line emission workload."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def xs():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2105_14782_gb300 import xs as m
+    return m
+
+
+def dev(a):
+    return torch.as_tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def check(xs, lines, nu_min, nu_max, N, T, P, n_gamma, tol64=1e-10, tol32=1e-5):
+    import oracle
+    dl = xs.DeviceLines(lines)
+    n_fft = xs.modit_fft_length(nu_min, nu_max, N, dl)
+    assert n_fft == oracle.modit_fft_length(nu_min, nu_max, N, lines.nu_hat)
+    want = oracle.modit(lines, nu_min, nu_max, N, T, P, n_gamma=n_gamma, n_fft=n_fft)
+    scale = np.abs(want).max(axis=1, keepdims=True)
+    for prec, tol in ((xs.PREC_FP64, tol64), (xs.PREC_MIXED, tol32)):
+        got = xs.modit_compute(dl, nu_min, nu_max, N, dev(T), dev(P), n_gamma=n_gamma, prec=prec).double().cpu().numpy()
+        err = np.abs(got - want) / scale
+        assert err.max() < tol, (prec, err.max())
+    return dl, n_fft
+
+
+def test_small_case_with_lines_beyond_the_grid(xs):
+    lines = W.water_like(3000, seed=31, nu_min=4355.0, nu_max=4375.0)
+    P = np.array([1e-3, 0.05, 1.0, 30.0])
+    T = 1300.0 * P ** 0.1
+    check(xs, lines, 4362.0, 4368.0, 3001, T, P, n_gamma=12)
+
+
+def test_single_gamma_node_and_narrow_band(xs):
+    lines = W.co_like(500, seed=32, n_bands=2, nu_min=4364.0, nu_max=4366.0)
+    check(xs, lines, 4363.0, 4367.0, 2048, np.array([900.0]), np.array([0.2]), n_gamma=1)
+
+
+def test_emission_size_three_layers(xs):
+    atm = W.emission_case()
+    idx = np.array([0, 50, 99])
+    P = atm.p_bar[idx]
+    T = 1300.0 * P ** 0.1
+    nu = atm.nu
+    check(xs, atm.species[0], float(nu[0]), float(nu[-1]), nu.size, T, P, n_gamma=16)
+
+
+def test_deterministic_and_empty(xs):
+    lines = W.water_like(800, seed=33, nu_min=4360.0, nu_max=4370.0)
+    dl = xs.DeviceLines(lines)
+    T, P = dev([1100.0, 1500.0]), dev([0.01, 3.0])
+    a = xs.modit_compute(dl, 4361.0, 4369.0, 4000, T, P)
+    b = xs.modit_compute(dl, 4361.0, 4369.0, 4000, T, P)
+    assert torch.equal(a, b)
+    empty = xs.DeviceLines(lines.subset(np.array([], dtype=np.int64)))
+    z = xs.modit_compute(empty, 4361.0, 4369.0, 4000, T, P, n_fft=8192)
+    assert torch.count_nonzero(z).item() == 0
+
+
+def test_rejects_bad_arguments(xs):
+    import ctypes as C
+    lines = xs.DeviceLines(W.water_like(10, seed=34, nu_min=4364.0, nu_max=4366.0))
+    s = lines.struct()
+    T, P = dev([1000.0]), dev([1.0])
+    out = torch.empty(100, dtype=torch.float64, device="cuda")
+    ws = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    f = xs.lib().modit_compute
+    args = lambda nfft, ng: (C.byref(s), 4364.0, 4366.0, 100, xs._dev(T), xs._dev(P), 1, 1.0, ng, nfft, 0,
+                             xs._dev(out), xs._dev(ws), ws.numel(), None)
+    assert f(*args(1000, 4)) == xs.XS_EINVAL  # not a power of two
+    assert f(*args(64, 4)) == xs.XS_EINVAL    # shorter than the grid
+    assert f(*args(256, 33)) == xs.XS_EINVAL  # too many gamma nodes
+    assert f(*args(1 << 24, 16)) == xs.XS_EINVAL  # workspace too small
