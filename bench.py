@@ -241,6 +241,68 @@ def serving(dev, closed_s, open_s):
             "latency": "submit to result on the host (pinned D2H of logL and gradient done)"}
 
 
+def modit_stats(dev, atm, scale_case=False):
+    """MODIT (Sec. 2.1.2) cross-sections of both species over all layers at theta*,
+    FP64 and FP32, timed with CUDA events, against the line-by-line sum (mixed,
+    W = 25 cm^-1) where that is above 1e-3 of its layer maximum."""
+    import torch
+    from paper_2105_14782_gb300 import xs
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            r = fn()
+        b.record()
+        torch.cuda.synchronize(dev)
+        return a.elapsed_time(b) / reps, r
+
+    f64 = dict(dtype=torch.float64, device=dev)
+    P = torch.as_tensor(atm.p_bar, **f64)
+    T = torch.as_tensor(W.THETA_STAR[0] * atm.p_bar ** W.THETA_STAR[1], **f64)
+    nu = torch.as_tensor(atm.nu, **f64)
+    nu_min, nu_max, N = float(atm.nu[0]), float(atm.nu[-1]), len(atm.nu)
+    res = {"n_gamma": 16, "layers": len(atm.p_bar), "grid": N}
+    lines = [xs.DeviceLines(sp, dev) for sp in atm.species]
+    res["lines"] = [dl.n for dl in lines]
+    res["n_fft"] = [xs.modit_fft_length(nu_min, nu_max, N, dl) for dl in lines]
+    out = {}
+    for name, prec in (("fp64", xs.PREC_FP64), ("fp32", xs.PREC_MIXED)):
+        ms = 0.0
+        sig = []
+        for dl, nf in zip(lines, res["n_fft"]):
+            ws = torch.empty(xs.lib().modit_workspace_bytes(dl.n, len(atm.p_bar), 16, nf, prec), dtype=torch.uint8,
+                             device=dev)
+            t, r = timed(lambda: xs.modit_compute(dl, nu_min, nu_max, N, T, P, n_gamma=16, n_fft=nf, prec=prec,
+                                                  workspace=ws))
+            ms += t
+            sig.append(r.double())
+            del ws
+        out[name] = (ms, sig)
+    res["fp64_ms"], res["fp32_ms"] = out["fp64"][0], out["fp32"][0]
+    if not scale_case:
+        ms = 0.0
+        lpf = []
+        for dl in lines:
+            t, r = timed(lambda: xs.xs_compute(dl, nu, T, P, prec=xs.PREC_MIXED))
+            ms += t
+            lpf.append(r.double())
+        res["lpf_mixed_ms"] = ms
+        d = []
+        for m, l in zip(out["fp64"][1], lpf):
+            mask = l > 1e-3 * l.max(dim=1, keepdim=True).values
+            d.append(((m - l).abs() / l)[mask])
+        d = torch.cat(d)
+        res["vs_lpf_rel_diff"] = {"median": float(d.median()), "p99": float(d.sort().values[int(0.99 * (d.numel() - 1))]),
+                                  "where": "sigma_LPF > 1e-3 of the layer maximum; LPF cut at 25 cm^-1, MODIT uncut"}
+    d32 = torch.cat([((a - b).abs() / b.abs().amax(dim=1, keepdim=True)).flatten()
+                     for a, b in zip(out["fp32"][1], out["fp64"][1])])
+    res["fp32_vs_fp64_max_rel_to_layer_max"] = float(d32.max())
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -251,6 +313,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison forward")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-modit", action="store_true", help="skip the MODIT measurement")
+    ap.add_argument("--modit-scale", action="store_true",
+                    help="also time MODIT on 10,000,000 + 200,000 lines and a 100,000-point grid")
     ap.add_argument("--layers", type=int, default=100,
                     help="layer count of the emission workload (100; fewer only for small profiling cases)")
     ap.add_argument("--serve-seconds", type=float, nargs=2, default=(15.0, 30.0),
@@ -415,6 +480,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(atm)
 
+    modit = None
+    if rank == 0 and world == 1 and not args.no_modit:
+        modit = {"emission": modit_stats(dev, atm)}
+        if args.modit_scale:
+            cfg = W.WORKLOADS["scale"]
+            p_, dp_ = W.pressure_layers(cfg["n_layers"])
+            big = W.Atmosphere(species=[W.water_like(cfg["n_water"]), W.co_like(cfg["n_co"])], vmr=[1e-3, 5e-4],
+                               nu=W.grid_lognu(cfg["n_grid"]), p_bar=p_, dp_bar=dp_)
+            modit["scale"] = modit_stats(dev, big, scale_case=True)
+        torch.cuda.empty_cache()
+
     serve_stats = None
     if rank == 0 and world == 1 and not args.no_serve:
         del model
@@ -438,7 +514,7 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
                 "gpu_launches": launches,
                 "kernel_ms_per_step": {"linesum_fwd": per_step_fwd, "linesum_adj": per_step_adj},
-                "fp64_path": fp64, "serving": serve_stats}
+                "fp64_path": fp64, "serving": serve_stats, "modit": modit}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

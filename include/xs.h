@@ -272,7 +272,7 @@ int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, 
  * workspace below modit_workspace_bytes; XS_ETOOBIG if cuFFT asks for more work
  * area than the workspace reserves; XS_ECUDA on launch or cuFFT failure.
  */
-size_t modit_workspace_bytes(int32_t L, int32_t n_gamma, int64_t n_fft, int prec);
+size_t modit_workspace_bytes(int64_t n_lines, int32_t L, int32_t n_gamma, int64_t n_fft, int prec);
 int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N, const double* T,
                   const double* P_bar, int32_t L, double broad_scale, int32_t n_gamma, int64_t n_fft, int prec,
                   void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream);

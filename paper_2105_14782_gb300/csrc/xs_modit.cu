@@ -3,13 +3,14 @@
 //
 // Grid: nu_i = nu_min exp(i/R0), i = 0..N-1, R0 = (N-1)/ln(nu_max/nu_min), so the
 // variable q = R0 ln(nu/nu_min) steps by 1.  For each layer:
-//   1. every line's S(T) (Eq. Slog) and normalised width gamma' = R0 gamma/nu_hat;
-//      per layer the min and max of gamma' (modit_range_kernel);
-//   2. the lineshape distribution S[k][j]: each line adds S to the two q nodes
-//      around q_l = R0 ln(nu_hat/nu_min) and the two ln gamma' nodes around its
-//      width, with linear weights (modit_lsd_kernel).  One thread per q node
-//      gathers the lines in [j-1, j+1) by binary search on the sorted centres, so
-//      the sum has a fixed order (no atomics);
+//   1. per layer the min and max of the normalised width gamma' = R0 gamma/nu_hat
+//      (modit_range_kernel); per line, once, q_l = R0 ln(nu_hat/nu_min) and the
+//      layer-independent parts of S(T) and ln gamma' (modit_prepass_kernel);
+//   2. the lineshape distribution S[k][j]: each line adds S(T) (Eq. Slog) to the
+//      two q nodes around q_l and the two ln gamma' nodes around its width, with
+//      linear weights (modit_lsd_kernel).  One thread per q node gathers the lines
+//      with q_l in [j-1, j+1) by binary search, so the sum has a fixed order (no
+//      atomics);
 //   3. batched real FFTs of the n_gamma rows (cuFFT);
 //   4. Y[f] = sum_k FT(S_k)[f] K_k[f], K_k = exp(-2 pi^2 beta'^2 f^2)
 //      (exp(-2 pi gamma'_k |f|) - gamma'_k DFT(A)[f]), beta' = R0 beta/nu_hat (common
@@ -36,20 +37,6 @@ constexpr int MODIT_THREADS = 256;
 template <class R> struct CplxOf;
 template <> struct CplxOf<double> { using type = cufftDoubleComplex; };
 template <> struct CplxOf<float> { using type = cufftComplex; };
-
-// S(T) (Eq. Slog, scaled) and gamma (Eq. gammahitran, reduced) of one line.
-__device__ __forceinline__ void modit_line(const double* __restrict__ nu_hat, const double* __restrict__ ln_S0,
-                                           const double* __restrict__ elower, const double* __restrict__ gamma_ref,
-                                           const double* __restrict__ n_temp, int64_t l, double qexp, double Tn,
-                                           double Pn, double sb, double scale, double* S, double* gam)
-{
-    const double nuh = nu_hat[l];
-    const double lnTr = log(Tn / Tref);
-    const double boltz = exp(ln_S0[l] - c2 * elower[l] * (1.0 / Tn - 1.0 / Tref) - qexp * lnTr);
-    const double stim = expm1(-c2 * nuh / Tn) / expm1(-c2 * nuh / Tref);
-    *S = boltz * stim * scale;
-    *gam = sb * gamma_ref[l] * exp(-n_temp[l] * lnTr) * (Pn / bar_per_atm);
-}
 
 __global__ void modit_range_init_kernel(unsigned long long* range, int L)
 {
@@ -86,6 +73,20 @@ __global__ void modit_range_kernel(const double* __restrict__ nu_hat, const doub
     }
 }
 
+// Layer-independent per-line terms: q = R0 ln(nu_hat/nu_min), the stimulated-
+// emission denominator expm1(-c2 nu_hat/296) and ln(R0 gamma_ref/nu_hat).
+__global__ void modit_prepass_kernel(const double* __restrict__ nu_hat, const double* __restrict__ gamma_ref,
+                                     int64_t nl, double nu_min, double R0, double* __restrict__ qv,
+                                     double* __restrict__ sden, double* __restrict__ lgref)
+{
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= nl) return;
+    const double nuh = nu_hat[l];
+    qv[l] = R0 * log(nuh / nu_min);
+    sden[l] = expm1(-c2 * nuh / Tref);
+    lgref[l] = log(R0 * gamma_ref[l] / nuh);
+}
+
 __device__ __forceinline__ int64_t first_at_least(const double* v, int64_t n, double x) // first i with v[i] >= x
 {
     int64_t lo = 0, hi = n;
@@ -98,43 +99,48 @@ __device__ __forceinline__ int64_t first_at_least(const double* v, int64_t n, do
 
 // One thread per (layer, slot): node j = slot, or slot - M for the left padding.
 // Lines with floor(q_l) == j give weight 1 - w, those with floor(q_l) == j - 1
-// give w (w = q_l - floor(q_l)); the candidates come from a binary search with a
-// half-node margin, the decision from each line's own q_l.
+// give w (w = q_l - floor(q_l)); they are found by binary search on the
+// (monotone) q_l of the prepass.  Per line and layer: S(T) (Eq. Slog) from one
+// exp and one expm1, ln gamma' from the prepass by FMAs.
 template <class R>
 __global__ void __launch_bounds__(MODIT_THREADS) modit_lsd_kernel(
     const double* __restrict__ nu_hat, const double* __restrict__ ln_S0, const double* __restrict__ elower,
-    const double* __restrict__ gamma_ref, const double* __restrict__ n_temp, int64_t nl, double qexp,
-    const double* __restrict__ T, const double* __restrict__ P, double sb, double scale, double nu_min, double R0,
-    int64_t N, int64_t M, int ng, const unsigned long long* __restrict__ range, R* __restrict__ lsd)
+    const double* __restrict__ n_temp, const double* __restrict__ qv, const double* __restrict__ sden,
+    const double* __restrict__ lgref, int64_t nl, double qexp, const double* __restrict__ T,
+    const double* __restrict__ P, double sb, double scale, int64_t N, int64_t M, int ng,
+    const unsigned long long* __restrict__ range, R* __restrict__ lsd)
 {
     const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int n = blockIdx.y;
     if (s >= M) return;
     const int64_t j = (s < (M + N) / 2) ? s : s - M;
-    const double Tn = T[n], Pn = P[n];
+    const double Tn = T[n];
+    const double lnTr = log(Tn / Tref);
+    const double bT = 1.0 / Tn - 1.0 / Tref;
+    const double lgP = log(sb * P[n] / bar_per_atm);
     const double gmin = __longlong_as_double((long long)range[2 * n]);
     const double gmax = __longlong_as_double((long long)range[2 * n + 1]);
     const double lg0 = log(gmin);
     const double dlg = (ng >= 2 && gmax > gmin) ? (log(gmax) - lg0) / (double)(ng - 1) : 0.0;
+    const double idlg = dlg > 0.0 ? 1.0 / dlg : 0.0;
     double acc[MODIT_MAX_GAMMA];
 #pragma unroll
     for (int k = 0; k < MODIT_MAX_GAMMA; ++k) acc[k] = 0.0;
-    const int64_t b = first_at_least(nu_hat, nl, nu_min * exp(((double)j - 1.5) / R0));
-    const int64_t e = first_at_least(nu_hat, nl, nu_min * exp(((double)j + 1.5) / R0));
+    const int64_t b = first_at_least(qv, nl, (double)(j - 1));
+    const int64_t e = first_at_least(qv, nl, (double)(j + 1));
     for (int64_t l = b; l < e; ++l) {
-        const double q = R0 * log(nu_hat[l] / nu_min);
+        const double q = qv[l];
         const double fq = floor(q);
         double wq;
         if (fq == (double)j) wq = 1.0 - (q - fq);
         else if (fq == (double)(j - 1)) wq = q - fq;
         else continue;
-        double S, gam;
-        modit_line(nu_hat, ln_S0, elower, gamma_ref, n_temp, l, qexp, Tn, Pn, sb, scale, &S, &gam);
-        const double g = R0 * gam / nu_hat[l];
+        const double S = exp(ln_S0[l] - c2 * elower[l] * bT - qexp * lnTr) *
+                         (expm1(-c2 * nu_hat[l] / Tn) / sden[l]) * scale;
         int k0 = 0;
         double wk = 0.0;
         if (dlg > 0.0) {
-            const double t = (log(g) - lg0) / dlg;
+            const double t = (lgref[l] + lgP - n_temp[l] * lnTr - lg0) * idlg;
             k0 = min(max((int)floor(t), 0), ng - 2);
             wk = t - (double)k0;
         }
@@ -223,10 +229,10 @@ using namespace xsd;
 size_t al256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct ModitPlan {
-    size_t range, lsd, Z, A, Ahat, Y, work, total, work_bytes;
+    size_t range, lines, lsd, Z, A, Ahat, Y, work, total, work_bytes;
 };
 
-ModitPlan modit_plan(int32_t L, int32_t ng, int64_t M, int prec)
+ModitPlan modit_plan(int64_t nl, int32_t L, int32_t ng, int64_t M, int prec)
 {
     const size_t rs = (prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
     const size_t H = (size_t)M / 2 + 1;
@@ -238,6 +244,7 @@ ModitPlan modit_plan(int32_t L, int32_t ng, int64_t M, int prec)
         return o;
     };
     p.range = take(2 * sizeof(unsigned long long) * (size_t)L);
+    p.lines = take(3 * sizeof(double) * (size_t)std::max<int64_t>(nl, 1)); // q, stim denominator, ln gamma'_ref
     p.lsd = take(rs * (size_t)L * ng * M); // reused for the inverse transforms' output
     p.Z = take(2 * rs * (size_t)L * ng * H);
     p.A = take(rs * (size_t)M);
@@ -333,11 +340,16 @@ int run_modit(const xs_lines* ln, double nu_min, double nu_max, int64_t N, const
     modit_range_init_kernel<<<(L + 255) / 256, 256, 0, st>>>(range, L);
     modit_range_kernel<<<dim3((unsigned)((nl + 255) / 256), (unsigned)L), 256, 0, st>>>(
         ln->nu_hat, ln->gamma_ref, ln->n_temp, nl, T, P, sb, R0, range);
+    double* qv = (double*)(ws + p.lines);
+    double* sden = qv + nl;
+    double* lgref = sden + nl;
+    modit_prepass_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, ln->gamma_ref, nl, nu_min, R0, qv,
+                                                                        sden, lgref);
     modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 1) / MODIT_THREADS), (unsigned)L), MODIT_THREADS, 0,
-                          st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->gamma_ref, ln->n_temp, nl, ln->q_exponent,
-                                T, P, sb, scale, nu_min, R0, N, M, ng, range, lsd);
+                          st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->n_temp, qv, sden, lgref, nl, ln->q_exponent,
+                                T, P, sb, scale, N, M, ng, range, lsd);
     modit_images_kernel<R><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, A);
-    xsi::count_launch(4);
+    xsi::count_launch(5);
     if (cudaGetLastError() != cudaSuccess) return XS_ECUDA;
     int r = fft_exec<R>(M, (int64_t)L * ng, true, lsd, Z, work, p.work_bytes, st);
     if (r != XS_OK) return r;
@@ -360,11 +372,11 @@ bool pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
 
 extern "C" {
 
-size_t modit_workspace_bytes(int32_t L, int32_t n_gamma, int64_t n_fft, int prec)
+size_t modit_workspace_bytes(int64_t n_lines, int32_t L, int32_t n_gamma, int64_t n_fft, int prec)
 {
-    if (L <= 0 || n_gamma < 1 || n_gamma > MODIT_MAX_GAMMA || !pow2(n_fft)) return 0;
+    if (n_lines < 0 || L <= 0 || n_gamma < 1 || n_gamma > MODIT_MAX_GAMMA || !pow2(n_fft)) return 0;
     if (prec != XS_PREC_FP64 && prec != XS_PREC_MIXED) return 0;
-    return modit_plan(L, n_gamma, n_fft, prec).total;
+    return modit_plan(n_lines, L, n_gamma, n_fft, prec).total;
 }
 
 int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N, const double* T,
@@ -377,7 +389,7 @@ int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N
     if (!(nu_min > 0.0) || !(nu_max > nu_min) || !(broad_scale > 0.0) || !(lines->mass_amu > 0.0)) return XS_EINVAL;
     if (n_gamma < 1 || n_gamma > MODIT_MAX_GAMMA || !pow2(n_fft) || n_fft < N + 2) return XS_EINVAL;
     if (prec != XS_PREC_FP64 && prec != XS_PREC_MIXED) return XS_EINVAL;
-    const ModitPlan p = modit_plan(L, n_gamma, n_fft, prec);
+    const ModitPlan p = modit_plan(lines->n, L, n_gamma, n_fft, prec);
     if (workspace_bytes < p.total) return XS_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
     if (prec == XS_PREC_FP64)

@@ -81,7 +81,7 @@ def lib():
                                       C.POINTER(C.c_int64)]
         L.xs_launch_count.restype = C.c_uint64
         L.modit_workspace_bytes.restype = sz
-        L.modit_workspace_bytes.argtypes = [i32, i32, i64, i]
+        L.modit_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
         L.modit_compute.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, sz, vp]
         _lib = L
     return _lib
@@ -186,7 +186,7 @@ def modit_compute(lines: DeviceLines, nu_min, nu_max, N, T, P_bar, broad_scale=1
     if out is None:
         out = torch.empty((L, N), dtype=dt, device=T.device)
     if workspace is None:
-        workspace = _ws(lib().modit_workspace_bytes(L, n_gamma, n_fft, prec), T.device)
+        workspace = _ws(lib().modit_workspace_bytes(lines.n, L, n_gamma, n_fft, prec), T.device)
     s = lines.struct()
     _check("modit_compute", lib().modit_compute(C.byref(s), float(nu_min), float(nu_max), N, _dev(T), _dev(P_bar), L,
                                                 float(broad_scale), n_gamma, n_fft, prec, _dev(out),
