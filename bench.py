@@ -41,8 +41,8 @@ FLOPS_PER_EVAL = {"fwd": 8, "adj": 12}  # cheapest packed wing forms (FFMA = 2, 
 # DRAM bytes (read + write) per launch of linesum_adjoint_kernel<float>, averaged over
 # the two species, from one ncu capture of the 20-layer case scaled to 100 layers
 # (the traffic is per layer); valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "linesum_adjoint_kernel<float>", "bytes_per_launch_100_layers": 2.800e9,
-           "sources_sha256": "e22d567ece65ec048c30cc997db3ef35959ccbf8c760de69bd4176824563a821"}
+TRAFFIC = {"kernel": "linesum_adjoint_kernel<float>", "bytes_per_launch_100_layers": 5.740e9,
+           "sources_sha256": "f979dda3e1932e5b9883687661ed759bd3f563fe8a9cc493b22628d5b67d73cd"}
 
 
 def kernel_sources_sha256():
