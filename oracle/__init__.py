@@ -312,3 +312,50 @@ def modit(lines, nu_min, nu_max, N, T, P_bar, sb=1.0, n_gamma=16, n_fft=None):
         y = np.fft.irfft(Y, n=n_fft)
         out[n] = y[:N] * R0 / nu
     return out
+
+
+# ------------------------------------------------------------------ responses (Sec. 4)
+
+C_KMS = 299792.458  # speed of light in km/s (velocities of Sec. 4 are in km/s)
+
+
+def rotation_zeta(x, u1, u2):
+    """Rigid-rotation kernel of Sec. 4.1: zeta(x) = int I dy / int int I dx dy over the
+    unit disk, I = 1 - u1 (1 - mu) - u2 (1 - mu)^2, mu = sqrt(1 - x^2 - y^2),
+    written out from that definition with s = sqrt(1 - x^2):
+      int I dy = 2s (1 - u1 - u2) + (pi/2) (u1 + 2 u2) s^2 - (4/3) u2 s^3,
+      int int I = pi (1 - u1/3 - u2/6).   Zero for |x| >= 1."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.sqrt(np.clip(1.0 - x * x, 0.0, None))
+    num = 2.0 * s * (1.0 - u1 - u2) + 0.5 * np.pi * (u1 + 2.0 * u2) * s ** 2 - (4.0 / 3.0) * u2 * s ** 3
+    return np.where(np.abs(x) < 1.0, num / (np.pi * (1.0 - u1 / 3.0 - u2 / 6.0)), 0.0)
+
+
+def gauss_ip(v, beta):
+    """Gaussian instrumental profile of Sec. 4.2 with standard deviation beta (km/s)."""
+    v = np.asarray(v, dtype=np.float64)
+    return np.exp(-0.5 * (v / beta) ** 2) / (np.sqrt(2.0 * np.pi) * beta)
+
+
+def response(F0, nu, nu_out, kernel, rv=0.0):
+    """Eq. responsenu: F(nu'_i) = sum_j k(c ln(nu'_i/nu_j) + RV) F0_j / sum_j k(c ln(nu'_i/nu_j)),
+    every pair summed (dense)."""
+    F0 = np.asarray(F0, dtype=np.float64)
+    dv = C_KMS * np.log(np.asarray(nu_out, dtype=np.float64)[:, None] / np.asarray(nu, dtype=np.float64)[None, :])
+    return (kernel(dv + rv) @ F0) / kernel(dv).sum(axis=1)
+
+
+def response_matrix(nu, nu_out, kernel, rv=0.0):
+    """The matrix of Eq. responsenu: F = A F0 (its transpose is the adjoint in F0)."""
+    dv = C_KMS * np.log(np.asarray(nu_out, dtype=np.float64)[:, None] / np.asarray(nu, dtype=np.float64)[None, :])
+    return kernel(dv + rv) / kernel(dv).sum(axis=1)[:, None]
+
+
+def rotation(F0, nu, vsini, u1, u2):
+    """Rotational broadening on the same grid (Sec. 4.1 with Eq. responsenu, RV = 0)."""
+    return response(F0, nu, nu, lambda v: rotation_zeta(v / vsini, u1, u2))
+
+
+def ip_rv(F1, nu, nu_out, beta, rv):
+    """Gaussian instrumental profile and radial velocity onto the output grid (Sec. 4.2, Eq. responsenu)."""
+    return response(F1, nu, nu_out, lambda v: gauss_ip(v, beta), rv)
