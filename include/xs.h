@@ -278,6 +278,37 @@ int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N
                   void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream);
 
 /*
+ * Astronomical and instrumental responses (Sec. 4, Eq. responsenu):
+ *   F(nu'_i) = sum_j k(c ln(nu'_i/nu_j) + RV) F0_j / sum_j k(c ln(nu'_i/nu_j)),
+ * velocities in km/s, c = 299792.458 km/s, grids increasing (device arrays).
+ * response_rotation: rigid rotation (Sec. 4.1) on the same grid, k(v) = zeta(v/vsini)
+ *   with quadratic limb darkening (u1, u2); zeta is taken from its disk-integral
+ *   definition, (2s(1-u1-u2) + (pi/2)(u1+2u2)s^2 - (4/3)u2 s^3)/(pi(1-u1/3-u2/6)),
+ *   s = sqrt(1-x^2) (the printed closed form does not integrate to one).
+ *   F0, F1 [N].
+ * response_ip_rv: Gaussian instrumental profile of standard deviation beta (Sec. 4.2;
+ *   beta = c/(2 sqrt(2 ln 2) R) for resolving power R) and radial velocity rv, from
+ *   the grid nu [N] onto nu_out [N_out]; the Gaussian is summed over |v| <= 10 beta.
+ *   nu_out must lie inside nu (every output needs kernel weight).
+ * The adjoints write g_F0 [N] (resp. g_F1 [N]) = transpose of the response applied
+ * to g_F1 [N] (resp. g_F [N_out]), and g_vsini [1] (resp. g_rv [1]) = the
+ * derivative of sum_i g_i F_i in vsini (resp. rv), device doubles, fixed-order
+ * sums.  They need response_workspace_bytes(number of outputs) of workspace.
+ * XS_EINVAL for bad arguments, XS_ECUDA on launch failure.
+ */
+int response_rotation(const double* F0, const double* nu, int64_t N, double vsini, double u1, double u2, double* F1,
+                      xs_stream stream);
+int response_ip_rv(const double* F1, const double* nu, int64_t N, const double* nu_out, int64_t N_out, double beta,
+                   double rv, double* F, xs_stream stream);
+size_t response_workspace_bytes(int64_t N_out);
+int response_rotation_adjoint(const double* g_F1, const double* F0, const double* nu, int64_t N, double vsini,
+                              double u1, double u2, double* g_F0, double* g_vsini, void* workspace,
+                              size_t workspace_bytes, xs_stream stream);
+int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu, int64_t N, const double* nu_out,
+                           int64_t N_out, double beta, double rv, double* g_F1, double* g_rv, void* workspace,
+                           size_t workspace_bytes, xs_stream stream);
+
+/*
  * Diagnostics (no paper counterpart).  xs_profile(1) makes the library record a
  * CUDA event pair around every line-sum kernel launch (forward and adjoint,
  * on the launching stream) until xs_profile(0); xs_profile_read synchronises

@@ -80,6 +80,12 @@ def lib():
         L.xs_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
         L.xs_launch_count.restype = C.c_uint64
+        L.response_rotation.argtypes = [vp, vp, i64, d, d, d, vp, vp]
+        L.response_ip_rv.argtypes = [vp, vp, i64, vp, i64, d, d, vp, vp]
+        L.response_workspace_bytes.restype = sz
+        L.response_workspace_bytes.argtypes = [i64]
+        L.response_rotation_adjoint.argtypes = [vp, vp, vp, i64, d, d, d, vp, vp, vp, sz, vp]
+        L.response_ip_rv_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, d, d, vp, vp, vp, sz, vp]
         L.modit_workspace_bytes.restype = sz
         L.modit_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
         L.modit_compute.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, sz, vp]
@@ -192,6 +198,42 @@ def modit_compute(lines: DeviceLines, nu_min, nu_max, N, T, P_bar, broad_scale=1
                                                 float(broad_scale), n_gamma, n_fft, prec, _dev(out),
                                                 _dev(workspace), workspace.numel(), _stream(stream)))
     return out
+
+
+def response_rotation(F0, nu, vsini, u1=0.0, u2=0.0, out=None, stream=None):
+    """Rigid-rotation broadening (Sec. 4.1) of F0 on its own grid nu (km/s)."""
+    out = torch.empty_like(F0) if out is None else out
+    _check("response_rotation", lib().response_rotation(_dev(F0), _dev(nu), nu.numel(), float(vsini), float(u1),
+                                                        float(u2), _dev(out), _stream(stream)))
+    return out
+
+
+def response_ip_rv(F1, nu, nu_out, beta, rv=0.0, out=None, stream=None):
+    """Gaussian instrumental profile (std beta, km/s) and radial velocity rv onto nu_out (Sec. 4.2)."""
+    out = torch.empty(nu_out.numel(), dtype=torch.float64, device=F1.device) if out is None else out
+    _check("response_ip_rv", lib().response_ip_rv(_dev(F1), _dev(nu), nu.numel(), _dev(nu_out), nu_out.numel(),
+                                                  float(beta), float(rv), _dev(out), _stream(stream)))
+    return out
+
+
+def response_rotation_adjoint(g_F1, F0, nu, vsini, u1=0.0, u2=0.0, stream=None):
+    g_F0 = torch.empty_like(F0)
+    g_v = torch.empty(1, dtype=torch.float64, device=F0.device)
+    ws = _ws(lib().response_workspace_bytes(nu.numel()), F0.device)
+    _check("response_rotation_adjoint", lib().response_rotation_adjoint(
+        _dev(g_F1), _dev(F0), _dev(nu), nu.numel(), float(vsini), float(u1), float(u2), _dev(g_F0), _dev(g_v),
+        _dev(ws), ws.numel(), _stream(stream)))
+    return g_F0, g_v
+
+
+def response_ip_rv_adjoint(g_F, F1, nu, nu_out, beta, rv=0.0, stream=None):
+    g_F1 = torch.empty_like(F1)
+    g_rv = torch.empty(1, dtype=torch.float64, device=F1.device)
+    ws = _ws(lib().response_workspace_bytes(nu_out.numel()), F1.device)
+    _check("response_ip_rv_adjoint", lib().response_ip_rv_adjoint(
+        _dev(g_F), _dev(F1), _dev(nu), nu.numel(), _dev(nu_out), nu_out.numel(), float(beta), float(rv), _dev(g_F1),
+        _dev(g_rv), _dev(ws), ws.numel(), _stream(stream)))
+    return g_F1, g_rv
 
 
 def _ptrs(ts):
