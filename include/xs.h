@@ -309,6 +309,21 @@ int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu
                            size_t workspace_bytes, xs_stream stream);
 
 /*
+ * The composite model as a vector-Jacobian product, for likelihoods that are not
+ * computed on the model grid (e.g. after the responses of Sec. 4 on an observed
+ * grid).  xs_model_forward_keep writes F0 [N] like xs_model_forward and keeps
+ * what the reverse sweep needs in the workspace; xs_model_vjp then writes
+ * out[1 .. 3 + S] = sum_j g_F0[j] dF0[j]/dtheta (theta's order) and out[0] = 0.
+ * xs_model_vjp must follow xs_model_forward_keep with the same model, theta and
+ * workspace, with the workspace untouched in between (stream-ordered).  d_obs
+ * and sig_obs of the model are not used.  Sizes, errors as xs_model_logl_grad.
+ */
+int xs_model_forward_keep(const xs_model* model, const double* theta, double* F0, void* workspace,
+                          size_t workspace_bytes, xs_stream stream);
+int xs_model_vjp(const xs_model* model, const double* theta, const double* g_F0, double* out, void* workspace,
+                 size_t workspace_bytes, xs_stream stream);
+
+/*
  * Diagnostics (no paper counterpart).  xs_profile(1) makes the library record a
  * CUDA event pair around every line-sum kernel launch (forward and adjoint,
  * on the launching stream) until xs_profile(0); xs_profile_read synchronises

@@ -358,35 +358,29 @@ int xs_model_forward(const xs_model* model, const double* theta, double* F0, voi
     return model_forward_impl(model, theta, F0, (char*)workspace, p, S(stream));
 }
 
-int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, double* F0, void* workspace,
-                       size_t workspace_bytes, xs_stream stream)
+} // extern "C"
+
+namespace {
+
+// Reverse sweep of the composite model from g_F = dlogL/dF0 (device [N]), after
+// a forward with XS_RUN_KEEP_ADJ in the same workspace: out[1 .. 3 + S] = dlogL/dtheta.
+int model_adjoint_impl(const xs_model* m, const double* theta, const double* gF, double* out, char* ws,
+                       const ModelPlan& p, cudaStream_t st)
 {
-    int r = check_model(m);
-    if (r) return r;
-    if (!theta || !out || !workspace || !m->d_obs || !m->sig_obs) return XS_EINVAL;
-    ModelPlan p = plan_model(m);
-    if (workspace_bytes < p.total) return XS_EINVAL;
-    if (!(theta[0] > 0.0) || !(theta[2 + m->n_species] > 0.0)) return XS_EINVAL;
-    cudaStream_t st = S(stream);
-    char* ws = (char*)workspace;
     const int Sp = m->n_species;
     const size_t LN = (size_t)m->L * (size_t)m->N;
     const size_t es = (m->prec == XS_PREC_MIXED) ? sizeof(float) : sizeof(double);
-    double* F = F0 ? F0 : (double*)(ws + p.F0);
-    r = model_forward_impl(m, theta, F, ws, p, st, xsi::XS_RUN_KEEP_ADJ);
-    if (r) return r;
     double* T = (double*)(ws + p.T);
     double* vmr = (double*)(ws + p.vmr);
     char* sig = ws + p.sigma;
     double* dtau = (double*)(ws + p.dtau);
-    double* gF = (double*)(ws + p.gF);
     double* gdtau = (double*)(ws + p.gdtau);
     double* gsig = (double*)(ws + p.gsig);
     double* gvmr = (double*)(ws + p.gvmr);
     double* gT = (double*)(ws + p.gT);
     double* gTtmp = (double*)(ws + p.gTtmp);
     double* gb = (double*)(ws + p.gb);
-    if ((r = xsi::rt_loglike(F, m->d_obs, m->sig_obs, m->N, out, gF, st))) return r;
+    int r;
     if ((r = xsi::rt_emission_adjoint(gF, dtau, T, m->nu, m->L, m->N, gdtau, gT, ws + p.emws, st))) return r;
     const void* sp[XS_MAX_SPECIES];
     double* gsp[XS_MAX_SPECIES];
@@ -405,6 +399,60 @@ int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, doub
     }
     return xsi::rt_theta_grad(Sp, m->L, theta[0], theta[1], theta + 2, theta[2 + Sp], T, m->P_bar, gT, gvmr, gb, out,
                               st);
+}
+
+int model_args(const xs_model* m, const double* theta, void* workspace, size_t workspace_bytes, ModelPlan* p)
+{
+    int r = check_model(m);
+    if (r) return r;
+    if (!theta || !workspace) return XS_EINVAL;
+    *p = plan_model(m);
+    if (workspace_bytes < p->total) return XS_EINVAL;
+    if (!(theta[0] > 0.0) || !(theta[2 + m->n_species] > 0.0)) return XS_EINVAL;
+    return XS_OK;
+}
+
+} // namespace
+
+extern "C" {
+
+int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, double* F0, void* workspace,
+                       size_t workspace_bytes, xs_stream stream)
+{
+    ModelPlan p;
+    int r = model_args(m, theta, workspace, workspace_bytes, &p);
+    if (r) return r;
+    if (!out || !m->d_obs || !m->sig_obs) return XS_EINVAL;
+    cudaStream_t st = S(stream);
+    char* ws = (char*)workspace;
+    double* F = F0 ? F0 : (double*)(ws + p.F0);
+    r = model_forward_impl(m, theta, F, ws, p, st, xsi::XS_RUN_KEEP_ADJ);
+    if (r) return r;
+    double* gF = (double*)(ws + p.gF);
+    if ((r = xsi::rt_loglike(F, m->d_obs, m->sig_obs, m->N, out, gF, st))) return r;
+    return model_adjoint_impl(m, theta, gF, out, ws, p, st);
+}
+
+int xs_model_forward_keep(const xs_model* m, const double* theta, double* F0, void* workspace,
+                          size_t workspace_bytes, xs_stream stream)
+{
+    ModelPlan p;
+    int r = model_args(m, theta, workspace, workspace_bytes, &p);
+    if (r) return r;
+    if (!F0) return XS_EINVAL;
+    return model_forward_impl(m, theta, F0, (char*)workspace, p, S(stream), xsi::XS_RUN_KEEP_ADJ);
+}
+
+int xs_model_vjp(const xs_model* m, const double* theta, const double* g_F0, double* out, void* workspace,
+                 size_t workspace_bytes, xs_stream stream)
+{
+    ModelPlan p;
+    int r = model_args(m, theta, workspace, workspace_bytes, &p);
+    if (r) return r;
+    if (!g_F0 || !out) return XS_EINVAL;
+    cudaStream_t st = S(stream);
+    if (cudaMemsetAsync(out, 0, sizeof(double), st) != cudaSuccess) return XS_ECUDA;
+    return model_adjoint_impl(m, theta, g_F0, out, (char*)workspace, p, st);
 }
 
 } // extern "C"

@@ -76,6 +76,8 @@ def lib():
         L.xs_model_workspace_bytes.argtypes = [C.POINTER(XsModelC)]
         L.xs_model_forward.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
         L.xs_model_logl_grad.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
+        L.xs_model_forward_keep.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
+        L.xs_model_vjp.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
         L.xs_profile.argtypes = [i]
         L.xs_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
@@ -369,6 +371,56 @@ class EmissionModel:
     def logl_grad(self, theta, stream=None):
         o = self.logl_grad_async(theta, stream=stream).cpu().numpy()
         return float(o[0]), o[1:].copy()
+
+
+    def forward_keep(self, theta, out=None, stream=None):
+        """F0 at theta, keeping the reverse sweep's state in the workspace (for vjp)."""
+        th = (C.c_double * len(theta))(*[float(v) for v in theta])
+        F0 = self.F0 if out is None else out
+        _check("xs_model_forward_keep", lib().xs_model_forward_keep(C.byref(self._c), th, _dev(F0), _dev(self.ws),
+                                                                    self.ws.numel(), _stream(stream)))
+        return F0
+
+    def vjp(self, theta, g_F0, stream=None):
+        """g_F0 . dF0/dtheta after forward_keep(theta): device tensor [3 + S]."""
+        th = (C.c_double * len(theta))(*[float(v) for v in theta])
+        _check("xs_model_vjp", lib().xs_model_vjp(C.byref(self._c), th, _dev(g_F0), _dev(self.out), _dev(self.ws),
+                                                  self.ws.numel(), _stream(stream)))
+        return self.out[1:]
+
+
+class ObservedModel:
+    """The model of Sec. 5's fit: emission F0 on the model grid, rigid rotation
+    (vsini, limb darkening u1, u2), Gaussian IP (beta) with radial velocity onto the
+    observed grid, Gaussian likelihood there (Eq. likelihood).  Parameters
+    theta = (T0, alpha, log10 vmr_0..log10 vmr_{S-1}, s_b, vsini, RV); the gradient
+    comes from the responses' adjoints and the composite model's vector-Jacobian
+    product."""
+
+    def __init__(self, model: EmissionModel, nu_obs, d_obs, sig_obs, beta, u1=0.0, u2=0.0):
+        f64 = dict(dtype=torch.float64, device=model.device)
+        self.m = model
+        self.nu_obs = torch.as_tensor(np.asarray(nu_obs), **f64)
+        self.d = torch.as_tensor(np.asarray(d_obs), **f64)
+        self.s = torch.as_tensor(np.asarray(sig_obs), **f64)
+        self.beta, self.u1, self.u2 = float(beta), float(u1), float(u2)
+        self.out = torch.empty(2, **f64)
+
+    def spectrum(self, theta, keep=False):
+        th, vsini, rv = list(theta[:-2]), float(theta[-2]), float(theta[-1])
+        F0 = self.m.forward_keep(th) if keep else self.m.forward(th)
+        F1 = response_rotation(F0, self.m.nu, vsini, self.u1, self.u2)
+        return F0, F1, response_ip_rv(F1, self.m.nu, self.nu_obs, self.beta, rv)
+
+    def logl_grad(self, theta):
+        th, vsini, rv = list(theta[:-2]), float(theta[-2]), float(theta[-1])
+        F0, F1, F = self.spectrum(theta, keep=True)
+        ll, gF = loglike_gauss(F, self.d, self.s)
+        gF1, g_rv = response_ip_rv_adjoint(gF, F1, self.m.nu, self.nu_obs, self.beta, rv)
+        gF0, g_vsini = response_rotation_adjoint(gF1, F0, self.m.nu, vsini, self.u1, self.u2)
+        g = self.m.vjp(th, gF0)
+        grad = torch.cat([g, g_vsini, g_rv]).cpu().numpy()
+        return float(ll.item()), grad
 
 
 class SpectrumLogL(torch.autograd.Function):
