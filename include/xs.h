@@ -309,6 +309,16 @@ int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu
                            size_t workspace_bytes, xs_stream stream);
 
 /*
+ * Layer-by-layer temperatures (the retrieval of Sec. 6 with one temperature per
+ * layer): as xs_model_logl_grad with the power law replaced by T [L] (device,
+ * Kelvin), log10_vmr [S] (host) and broad_scale; out [1 + L + S + 1] device:
+ * logL, dlogL/dT_n for every layer, dlogL/dlog10 vmr_m, dlogL/d broad_scale.
+ * A prior on the T_n (the paper's Gaussian process) is the caller's.
+ */
+int xs_model_logl_grad_layers(const xs_model* model, const double* T, const double* log10_vmr, double broad_scale,
+                              double* out, double* F0, void* workspace, size_t workspace_bytes, xs_stream stream);
+
+/*
  * The composite model as a vector-Jacobian product, for likelihoods that are not
  * computed on the model grid (e.g. after the responses of Sec. 4 on an observed
  * grid).  xs_model_forward_keep writes F0 [N] like xs_model_forward and keeps

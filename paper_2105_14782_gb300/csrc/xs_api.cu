@@ -309,8 +309,10 @@ ModelPlan plan_model(const xs_model* m)
     return p;
 }
 
+// theta = (T0, alpha, log10 vmr.., s_b); with T_given (device [L]) the layer
+// temperatures are those instead of the power law and theta[0], theta[1] unused.
 int model_forward_impl(const xs_model* m, const double* theta, double* F0out, char* ws, const ModelPlan& p,
-                       cudaStream_t st, int xs_flags = 0)
+                       cudaStream_t st, int xs_flags = 0, const double* T_given = nullptr)
 {
     const int Sp = m->n_species;
     const size_t LN = (size_t)m->L * (size_t)m->N;
@@ -319,8 +321,14 @@ int model_forward_impl(const xs_model* m, const double* theta, double* F0out, ch
     double* vmr = (double*)(ws + p.vmr);
     char* sig = ws + p.sigma;
     double* dtau = (double*)(ws + p.dtau);
-    int r = xsi::rt_temperatures(theta[0], theta[1], m->P_bar, m->L, T, st);
-    if (r) return r;
+    int r;
+    if (T_given) {
+        if (cudaMemcpyAsync(T, T_given, sizeof(double) * m->L, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return XS_ECUDA;
+    } else {
+        r = xsi::rt_temperatures(theta[0], theta[1], m->P_bar, m->L, T, st);
+        if (r) return r;
+    }
     r = xsi::rt_fill_vmr(nullptr, Sp, m->L, theta + 2, vmr, st);
     if (r) return r;
     const void* sp[XS_MAX_SPECIES];
@@ -365,7 +373,7 @@ namespace {
 // Reverse sweep of the composite model from g_F = dlogL/dF0 (device [N]), after
 // a forward with XS_RUN_KEEP_ADJ in the same workspace: out[1 .. 3 + S] = dlogL/dtheta.
 int model_adjoint_impl(const xs_model* m, const double* theta, const double* gF, double* out, char* ws,
-                       const ModelPlan& p, cudaStream_t st)
+                       const ModelPlan& p, cudaStream_t st, bool per_layer = false)
 {
     const int Sp = m->n_species;
     const size_t LN = (size_t)m->L * (size_t)m->N;
@@ -397,6 +405,7 @@ int model_adjoint_impl(const xs_model* m, const double* theta, const double* gF,
         if (r) return r;
         if ((r = xsi::rt_accumulate(gT, gTtmp, m->L, 0, st))) return r;
     }
+    if (per_layer) return xsi::rt_layer_grad(Sp, m->L, theta + 2, gT, gvmr, gb, out, st);
     return xsi::rt_theta_grad(Sp, m->L, theta[0], theta[1], theta + 2, theta[2 + Sp], T, m->P_bar, gT, gvmr, gb, out,
                               st);
 }
@@ -431,6 +440,30 @@ int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, doub
     double* gF = (double*)(ws + p.gF);
     if ((r = xsi::rt_loglike(F, m->d_obs, m->sig_obs, m->N, out, gF, st))) return r;
     return model_adjoint_impl(m, theta, gF, out, ws, p, st);
+}
+
+int xs_model_logl_grad_layers(const xs_model* m, const double* T, const double* log10_vmr, double broad_scale,
+                              double* out, double* F0, void* workspace, size_t workspace_bytes, xs_stream stream)
+{
+    if (!m || !T || !log10_vmr || m->n_species < 1 || m->n_species > XS_MAX_SPECIES) return XS_EINVAL;
+    // theta in the composite layout with placeholder T0 = 1, alpha = 0 (unused)
+    double theta[3 + XS_MAX_SPECIES];
+    theta[0] = 1.0;
+    theta[1] = 0.0;
+    for (int s = 0; s < m->n_species; ++s) theta[2 + s] = log10_vmr[s];
+    theta[2 + m->n_species] = broad_scale;
+    ModelPlan p;
+    int r = model_args(m, theta, workspace, workspace_bytes, &p);
+    if (r) return r;
+    if (!out || !m->d_obs || !m->sig_obs) return XS_EINVAL;
+    cudaStream_t st = S(stream);
+    char* ws = (char*)workspace;
+    double* F = F0 ? F0 : (double*)(ws + p.F0);
+    r = model_forward_impl(m, theta, F, ws, p, st, xsi::XS_RUN_KEEP_ADJ, T);
+    if (r) return r;
+    double* gF = (double*)(ws + p.gF);
+    if ((r = xsi::rt_loglike(F, m->d_obs, m->sig_obs, m->N, out, gF, st))) return r;
+    return model_adjoint_impl(m, theta, gF, out, ws, p, st, true);
 }
 
 int xs_model_forward_keep(const xs_model* m, const double* theta, double* F0, void* workspace,

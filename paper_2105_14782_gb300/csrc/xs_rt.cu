@@ -318,6 +318,24 @@ __global__ void theta_grad_kernel(int S, int L, double T0, VmrArgs a, const doub
     out[3 + S] = gb;
 }
 
+// Gradient for per-layer temperatures: out[1 + n] = dlogL/dT_n, then
+// dlogL/dlog10 vmr_m and dlogL/ds_b (out[0], logL, is left as it is).
+__global__ void layer_grad_kernel(int S, int L, VmrArgs a, const double* __restrict__ g_T,
+                                  const double* __restrict__ g_vmr, const double* __restrict__ g_b,
+                                  double* __restrict__ out)
+{
+    for (int n = threadIdx.x; n < L; n += blockDim.x) out[1 + n] = g_T[n];
+    if (threadIdx.x != 0) return;
+    double gb = 0.0;
+    for (int m = 0; m < S; ++m) {
+        double s = 0.0;
+        for (int n = 0; n < L; ++n) s += g_vmr[(size_t)m * L + n];
+        out[1 + L + m] = 2.30258509299404568402 * pow(10.0, a.lg[m]) * s;
+        gb += g_b[m];
+    }
+    out[1 + L + S] = gb;
+}
+
 __global__ void accumulate_kernel(double* __restrict__ dst, const double* __restrict__ src, int64_t n, int first)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -430,6 +448,15 @@ int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* l
     VmrArgs a{};
     for (int m = 0; m < S; ++m) a.lg[m] = lg[m];
     theta_grad_kernel<<<1, 32, 0, st>>>(S, L, T0, a, T, P, g_T, g_vmr, g_b, out);
+    return launched(1);
+}
+
+int rt_layer_grad(int32_t S, int32_t L, const double* lg, const double* g_T, const double* g_vmr, const double* g_b,
+                  double* out, cudaStream_t st)
+{
+    VmrArgs a{};
+    for (int m = 0; m < S; ++m) a.lg[m] = lg[m];
+    layer_grad_kernel<<<1, 128, 0, st>>>(S, L, a, g_T, g_vmr, g_b, out);
     return launched(1);
 }
 

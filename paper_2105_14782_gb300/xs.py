@@ -76,6 +76,8 @@ def lib():
         L.xs_model_workspace_bytes.argtypes = [C.POINTER(XsModelC)]
         L.xs_model_forward.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
         L.xs_model_logl_grad.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
+        L.xs_model_logl_grad_layers.argtypes = [C.POINTER(XsModelC), vp, C.POINTER(C.c_double), d, vp, vp, vp, sz,
+                                                vp]
         L.xs_model_forward_keep.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, sz, vp]
         L.xs_model_vjp.argtypes = [C.POINTER(XsModelC), C.POINTER(C.c_double), vp, vp, vp, sz, vp]
         L.xs_profile.argtypes = [i]
@@ -372,6 +374,18 @@ class EmissionModel:
         o = self.logl_grad_async(theta, stream=stream).cpu().numpy()
         return float(o[0]), o[1:].copy()
 
+
+    def logl_grad_layers(self, T, log10_vmr, broad_scale=1.0, stream=None):
+        """logL and its gradient in the per-layer temperatures T [L] (device tensor),
+        the log10 mixing ratios and the broadening scale: (logL, g_T [L], g_vmr [S], g_b)."""
+        lv = (C.c_double * self.S)(*[float(v) for v in log10_vmr])
+        o = torch.empty(2 + self.L + self.S, dtype=torch.float64, device=self.device)
+        T = torch.as_tensor(T, dtype=torch.float64, device=self.device).contiguous()
+        _check("xs_model_logl_grad_layers", lib().xs_model_logl_grad_layers(
+            C.byref(self._c), _dev(T), lv, float(broad_scale), _dev(o), None, _dev(self.ws), self.ws.numel(),
+            _stream(stream)))
+        o = o.cpu().numpy()
+        return float(o[0]), o[1:1 + self.L], o[1 + self.L:1 + self.L + self.S], float(o[1 + self.L + self.S])
 
     def forward_keep(self, theta, out=None, stream=None):
         """F0 at theta, keeping the reverse sweep's state in the workspace (for vjp)."""
