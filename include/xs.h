@@ -278,6 +278,21 @@ int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N
                   void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream);
 
 /*
+ * Reverse-mode adjoint of modit_compute (same grid, lines and arguments).  From
+ * g_sigma [L][N] (double, device) it writes g_T [L] = sum_j g_sigma[n][j]
+ * dsigma[n][j]/dT_n, through S(T), beta' and every line's and node's gamma', and
+ * g_broad [1] = the derivative in broad_scale (which moves all widths and both
+ * ends of the gamma' grid alike, so it acts through the kernels only).  The
+ * weights are piecewise linear in ln gamma', so the derivative is that of the
+ * piece in use.  The forward distribution is recomputed; sums in a fixed order.
+ */
+size_t modit_adjoint_workspace_bytes(int64_t n_lines, int32_t L, int32_t n_gamma, int64_t n_fft, int prec);
+int modit_compute_adjoint(const xs_lines* lines, double nu_min, double nu_max, int64_t N, const double* T,
+                          const double* P_bar, int32_t L, double broad_scale, int32_t n_gamma, int64_t n_fft,
+                          int prec, const double* g_sigma, double* g_T, double* g_broad, void* workspace,
+                          size_t workspace_bytes, xs_stream stream);
+
+/*
  * Astronomical and instrumental responses (Sec. 4, Eq. responsenu):
  *   F(nu'_i) = sum_j k(c ln(nu'_i/nu_j) + RV) F0_j / sum_j k(c ln(nu'_i/nu_j)),
  * velocities in km/s, c = 299792.458 km/s, grids increasing (device arrays).

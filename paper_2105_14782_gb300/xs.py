@@ -90,6 +90,10 @@ def lib():
         L.response_workspace_bytes.argtypes = [i64]
         L.response_rotation_adjoint.argtypes = [vp, vp, vp, i64, d, d, d, vp, vp, vp, sz, vp]
         L.response_ip_rv_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, d, d, vp, vp, vp, sz, vp]
+        L.modit_adjoint_workspace_bytes.restype = sz
+        L.modit_adjoint_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
+        L.modit_compute_adjoint.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, vp,
+                                            vp, sz, vp]
         L.modit_workspace_bytes.restype = sz
         L.modit_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
         L.modit_compute.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, sz, vp]
@@ -238,6 +242,23 @@ def response_ip_rv_adjoint(g_F, F1, nu, nu_out, beta, rv=0.0, stream=None):
         _dev(g_F), _dev(F1), _dev(nu), nu.numel(), _dev(nu_out), nu_out.numel(), float(beta), float(rv), _dev(g_F1),
         _dev(g_rv), _dev(ws), ws.numel(), _stream(stream)))
     return g_F1, g_rv
+
+
+def modit_compute_adjoint(lines: DeviceLines, nu_min, nu_max, N, T, P_bar, g_sigma, broad_scale=1.0, n_gamma=16,
+                          n_fft=None, prec=PREC_FP64, workspace=None, stream=None):
+    """(g_T [L], g_broad [1]) of sum(g_sigma * modit_compute(...))."""
+    L = T.numel()
+    if n_fft is None:
+        n_fft = modit_fft_length(nu_min, nu_max, N, lines)
+    g_T = torch.empty(L, dtype=torch.float64, device=T.device)
+    g_b = torch.empty(1, dtype=torch.float64, device=T.device)
+    if workspace is None:
+        workspace = _ws(lib().modit_adjoint_workspace_bytes(lines.n, L, n_gamma, n_fft, prec), T.device)
+    s = lines.struct()
+    _check("modit_compute_adjoint", lib().modit_compute_adjoint(
+        C.byref(s), float(nu_min), float(nu_max), N, _dev(T), _dev(P_bar), L, float(broad_scale), n_gamma, n_fft,
+        prec, _dev(g_sigma), _dev(g_T), _dev(g_b), _dev(workspace), workspace.numel(), _stream(stream)))
+    return g_T, g_b
 
 
 def _ptrs(ts):

@@ -84,3 +84,42 @@ def test_rejects_bad_arguments(xs):
     assert f(*args(64, 4)) == xs.XS_EINVAL    # shorter than the grid
     assert f(*args(256, 33)) == xs.XS_EINVAL  # too many gamma nodes
     assert f(*args(1 << 24, 16)) == xs.XS_EINVAL  # workspace too small
+
+
+def test_adjoint_matches_central_differences_of_the_oracle(xs):
+    import oracle
+    lines = W.water_like(800, seed=35, nu_min=4360.0, nu_max=4370.0)
+    nu_min, nu_max, N = 4362.0, 4368.0, 3001
+    P = np.array([0.01, 0.3, 3.0])
+    T = np.array([900.0, 1200.0, 1500.0])
+    sb, ng = 1.2, 8
+    dl = xs.DeviceLines(lines)
+    n_fft = xs.modit_fft_length(nu_min, nu_max, N, dl)
+    rng = np.random.default_rng(36)
+    g = rng.standard_normal((P.size, N)) * 1e20
+
+    def F(Tv, sbv):
+        return float(np.sum(g * oracle.modit(lines, nu_min, nu_max, N, Tv, P, sb=sbv, n_gamma=ng, n_fft=n_fft)))
+
+    def rich(f, x, h):
+        d1 = (f(x + h) - f(x - h)) / (2 * h)
+        d2 = (f(x + h / 2) - f(x - h / 2)) / h
+        return (4 * d2 - d1) / 3
+
+    fd_T = []
+    for n in range(P.size):
+        e = np.zeros(P.size)
+        e[n] = 1.0
+        fd_T.append(rich(lambda x: F(T + (x - T[n]) * e, sb), T[n], 1e-3))
+    fd_b = rich(lambda x: F(T, x), sb, 1e-6)
+    res = {}
+    for prec in (xs.PREC_FP64, xs.PREC_MIXED):
+        gT, gb = xs.modit_compute_adjoint(dl, nu_min, nu_max, N, dev(T), dev(P), dev(g), broad_scale=sb, n_gamma=ng,
+                                          n_fft=n_fft, prec=prec)
+        res[prec] = (gT.cpu().numpy(), gb.item())
+    gT, gb = res[xs.PREC_FP64]
+    np.testing.assert_allclose(gT, fd_T, rtol=1e-5)
+    assert gb == pytest.approx(fd_b, rel=1e-5)
+    gT32, gb32 = res[xs.PREC_MIXED]
+    np.testing.assert_allclose(gT32, gT, rtol=1e-3, atol=1e-4 * np.abs(gT).max())
+    assert gb32 == pytest.approx(gb, rel=1e-3)
