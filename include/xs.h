@@ -226,7 +226,17 @@ typedef struct {
     const double* d_obs;   /* [N] observed spectrum (may be NULL for forward-only use) */
     const double* sig_obs; /* [N] its 1-sigma errors */
     int prec;
+    /* Cross-section method.  XS_METHOD_LPF (0, the default of a zeroed struct):
+     * the line-by-line sum (xs_compute).  XS_METHOD_MODIT (1): modit_compute, which
+     * needs nu to be the log grid from nu_min to nu_max (N points) and per species
+     * the padded length n_fft[s]; wing_cut is not used. */
+    int method;
+    int32_t n_gamma;
+    double nu_min, nu_max;
+    int64_t n_fft[XS_MAX_SPECIES];
 } xs_model;
+
+enum { XS_METHOD_LPF = 0, XS_METHOD_MODIT = 1 };
 
 size_t xs_model_workspace_bytes(const xs_model* model);
 

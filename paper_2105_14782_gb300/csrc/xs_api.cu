@@ -267,6 +267,15 @@ int check_model(const xs_model* m)
     if (!(m->wing_cut > 0.0) || !(m->gravity > 0.0) || !(m->mu > 0.0) || !prec_ok(m->prec)) return XS_EINVAL;
     for (int s = 0; s < m->n_species; ++s)
         if (check_lines(&m->species[s])) return XS_EINVAL;
+    if (m->method != XS_METHOD_LPF && m->method != XS_METHOD_MODIT) return XS_EINVAL;
+    if (m->method == XS_METHOD_MODIT) {
+        if (m->n_gamma < 1 || m->n_gamma > 32 || !(m->nu_min > 0.0) || !(m->nu_max > m->nu_min) || m->N < 2)
+            return XS_EINVAL;
+        for (int s = 0; s < m->n_species; ++s) {
+            const int64_t M = m->n_fft[s];
+            if (M < m->N + 2 || (M & (M - 1)) != 0) return XS_EINVAL;
+        }
+    }
     return XS_OK;
 }
 
@@ -299,7 +308,12 @@ ModelPlan plan_model(const xs_model* m)
     // one full workspace per species, so the forward's line records stay valid
     // for the adjoint of the same call
     for (int s = 0; s < Sp; ++s) {
-        p.xsws_sp_bytes[s] = xs_workspace_bytes(m->species[s].n, m->N, m->L, m->prec);
+        if (m->method == XS_METHOD_MODIT)
+            p.xsws_sp_bytes[s] =
+                std::max(modit_workspace_bytes(m->species[s].n, m->L, m->n_gamma, m->n_fft[s], m->prec),
+                         modit_adjoint_workspace_bytes(m->species[s].n, m->L, m->n_gamma, m->n_fft[s], m->prec));
+        else
+            p.xsws_sp_bytes[s] = xs_workspace_bytes(m->species[s].n, m->N, m->L, m->prec);
         p.xsws_sp[s] = take(p.xsws_sp_bytes[s]);
     }
     p.xsws_bytes = p.xsws_sp_bytes[0];
@@ -334,9 +348,14 @@ int model_forward_impl(const xs_model* m, const double* theta, double* F0out, ch
     const void* sp[XS_MAX_SPECIES];
     for (int s = 0; s < Sp; ++s) {
         sp[s] = sig + es * LN * s;
-        r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec,
-                        (void*)sp[s], ws + p.xsws_sp[s], p.xsws_sp_bytes[s], false, nullptr, nullptr, nullptr, st,
-                        xs_flags);
+        if (m->method == XS_METHOD_MODIT)
+            r = modit_compute(&m->species[s], m->nu_min, m->nu_max, m->N, T, m->P_bar, m->L, theta[2 + Sp],
+                              m->n_gamma, m->n_fft[s], m->prec, (void*)sp[s], ws + p.xsws_sp[s], p.xsws_sp_bytes[s],
+                              st);
+        else
+            r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec,
+                            (void*)sp[s], ws + p.xsws_sp[s], p.xsws_sp_bytes[s], false, nullptr, nullptr, nullptr, st,
+                            xs_flags);
         if (r) return r;
     }
     r = xsi::rt_tau(sp, Sp, vmr, m->P_bar, m->dP_bar, m->L, m->N, m->gravity, m->mu, m->kappa_coef, m->prec, dtau, st);
@@ -400,8 +419,14 @@ int model_adjoint_impl(const xs_model* m, const double* theta, const double* gF,
                                  gvmr, st)))
         return r;
     for (int s = 0; s < Sp; ++s) {
-        r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec, nullptr,
-                        ws + p.xsws_sp[s], p.xsws_sp_bytes[s], true, gsp[s], gTtmp, gb + s, st, xsi::XS_RUN_REUSE);
+        if (m->method == XS_METHOD_MODIT)
+            r = modit_compute_adjoint(&m->species[s], m->nu_min, m->nu_max, m->N, T, m->P_bar, m->L, theta[2 + Sp],
+                                      m->n_gamma, m->n_fft[s], m->prec, gsp[s], gTtmp, gb + s, ws + p.xsws_sp[s],
+                                      p.xsws_sp_bytes[s], st);
+        else
+            r = xsi::xs_run(&m->species[s], m->nu, m->N, T, m->P_bar, m->L, theta[2 + Sp], m->wing_cut, m->prec,
+                            nullptr, ws + p.xsws_sp[s], p.xsws_sp_bytes[s], true, gsp[s], gTtmp, gb + s, st,
+                            xsi::XS_RUN_REUSE);
         if (r) return r;
         if ((r = xsi::rt_accumulate(gT, gTtmp, m->L, 0, st))) return r;
     }

@@ -40,7 +40,9 @@ class XsModelC(C.Structure):
     _fields_ = [("n_species", C.c_int32), ("species", XsLinesC * MAX_SPECIES), ("nu", C.c_void_p),
                 ("N", C.c_int64), ("P_bar", C.c_void_p), ("dP_bar", C.c_void_p), ("L", C.c_int32),
                 ("wing_cut", C.c_double), ("gravity", C.c_double), ("mu", C.c_double), ("kappa_coef", C.c_double),
-                ("d_obs", C.c_void_p), ("sig_obs", C.c_void_p), ("prec", C.c_int)]
+                ("d_obs", C.c_void_p), ("sig_obs", C.c_void_p), ("prec", C.c_int), ("method", C.c_int),
+                ("n_gamma", C.c_int32), ("nu_min", C.c_double), ("nu_max", C.c_double),
+                ("n_fft", C.c_int64 * MAX_SPECIES)]
 
 
 def lib():
@@ -340,9 +342,18 @@ class EmissionModel:
     resident on one GPU, with the composite forward and log-likelihood-gradient
     calls of libxs.  theta = (T0, alpha, log10 vmr_0..log10 vmr_{S-1}, s_b)."""
 
-    def __init__(self, atm, prec=PREC_MIXED, device="cuda", d_obs=None, sig_obs=None, lines=None):
+    def __init__(self, atm, prec=PREC_MIXED, device="cuda", d_obs=None, sig_obs=None, lines=None, method="lpf",
+                 n_gamma=16):
         self.device = torch.device(device)
         self.prec = prec
+        self.method, self.n_gamma = method, int(n_gamma)
+        if method == "modit":
+            nu = np.asarray(atm.nu, dtype=np.float64)
+            want = nu[0] * (nu[-1] / nu[0]) ** (np.arange(nu.size) / (nu.size - 1))
+            if not np.allclose(nu, want, rtol=1e-13, atol=0):
+                raise ValueError("MODIT needs the log grid nu_min (nu_max/nu_min)^(i/(N-1))")
+        elif method != "lpf":
+            raise ValueError(f"unknown cross-section method {method!r}")
         self.species = lines if lines is not None else [DeviceLines(sp, device) for sp in atm.species]
         f64 = dict(dtype=torch.float64, device=self.device)
         self.nu = torch.as_tensor(np.asarray(atm.nu), **f64)
@@ -362,6 +373,15 @@ class EmissionModel:
         sp = (XsLinesC * MAX_SPECIES)()
         for i, s in enumerate(self.species):
             sp[i] = s.struct()
+        c = self._struct_base(sp)
+        if self.method == "modit":
+            nu0, nu1 = float(self.atm.nu[0]), float(self.atm.nu[-1])
+            c.method, c.n_gamma, c.nu_min, c.nu_max = 1, self.n_gamma, nu0, nu1
+            for i, sp_ in enumerate(self.species):
+                c.n_fft[i] = modit_fft_length(nu0, nu1, self.N, sp_)
+        return c
+
+    def _struct_base(self, sp):
         a = self.atm
         return XsModelC(self.S, sp, self.nu.data_ptr(), self.N, self.P.data_ptr(), self.dP.data_ptr(), self.L,
                         float(a.wing_cut), float(a.gravity), float(a.mu), float(a.kappa_coef),

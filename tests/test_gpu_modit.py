@@ -123,3 +123,53 @@ def test_adjoint_matches_central_differences_of_the_oracle(xs):
     gT32, gb32 = res[xs.PREC_MIXED]
     np.testing.assert_allclose(gT32, gT, rtol=1e-3, atol=1e-4 * np.abs(gT).max())
     assert gb32 == pytest.approx(gb, rel=1e-3)
+
+
+def test_composite_model_with_modit(xs):
+    """Emission model whose cross-sections come from MODIT: spectrum and logL
+    against the same pipeline assembled from the oracle (MODIT, optical depth,
+    emission, likelihood), gradient against its Richardson differences."""
+    import math
+
+    import oracle
+    p, dp = W.pressure_layers(8)
+    nu = W.grid_lognu(1200, 4363.0, 4367.0)
+    atm = W.Atmosphere(species=[W.water_like(600, seed=37, nu_min=4361.0, nu_max=4369.0),
+                                W.co_like(150, seed=38, n_bands=2, nu_min=4361.0, nu_max=4369.0)],
+                       vmr=[1e-3, 5e-4], nu=nu, p_bar=p, dp_bar=dp)
+    ng = 8
+    m64 = xs.EmissionModel(atm, prec=xs.PREC_FP64, method="modit", n_gamma=ng)
+    nfft = [m64._c.n_fft[i] for i in range(2)]
+
+    def oracle_F(theta):
+        T = oracle.temperatures(theta[0], theta[1], p)
+        sig = [oracle.modit(sp, nu[0], nu[-1], nu.size, T, p, sb=theta[4], n_gamma=ng, n_fft=nf)
+               for sp, nf in zip(atm.species, nfft)]
+        vmr = np.array([[10.0 ** theta[2 + k]] * p.size for k in range(2)])
+        return oracle.emission(oracle.tau(sig, vmr, p, dp), T, nu)
+
+    ts = np.array([1300.0, 0.1, -3.0, math.log10(5e-4), 1.0])
+    Fs = oracle_F(ts)
+    sig = 0.01 * Fs
+    d = Fs + sig * W.std_normal(Fs.size)
+    theta = np.array([1250.0, 0.12, -2.8, -3.4, 1.3])
+    F_o = oracle_F(theta)
+    ll_o = float(oracle.loglike(F_o, d, sig))
+    fd = np.empty(5)
+    for i in range(5):
+        h = 1e-4 * abs(theta[i])
+        f = lambda x: float(oracle.loglike(oracle_F(np.concatenate([theta[:i], [x], theta[i + 1:]])), d, sig))
+        d1 = (f(theta[i] + h) - f(theta[i] - h)) / (2 * h)
+        d2 = (f(theta[i] + h / 2) - f(theta[i] - h / 2)) / h
+        fd[i] = (4 * d2 - d1) / 3
+    m64.set_observation(d, sig)
+    F = m64.forward(theta).cpu().numpy()
+    assert np.max(np.abs(F - F_o) / F_o) < 1e-10
+    ll, g = m64.logl_grad(theta)
+    assert ll == pytest.approx(ll_o, rel=1e-10)
+    np.testing.assert_allclose(g, fd, rtol=2e-5, atol=1e-8 * np.abs(fd).max())
+    mmx = xs.EmissionModel(atm, prec=xs.PREC_MIXED, method="modit", n_gamma=ng, d_obs=d, sig_obs=sig,
+                           lines=m64.species)
+    llm, gm = mmx.logl_grad(theta)
+    assert llm == pytest.approx(ll_o, rel=1e-4)
+    np.testing.assert_allclose(gm, g, rtol=2e-3, atol=1e-4 * np.abs(g).max())
