@@ -297,6 +297,16 @@ def modit_stats(dev, atm, scale_case=False):
         d = torch.cat(d)
         res["vs_lpf_rel_diff"] = {"median": float(d.median()), "p99": float(d.sort().values[int(0.99 * (d.numel() - 1))]),
                                   "where": "sigma_LPF > 1e-3 of the layer maximum; LPF cut at 25 cm^-1, MODIT uncut"}
+    # the HMC step with MODIT cross-sections: forward + gradient of the emission model
+    theta = W.theta_points(64)[0]
+    for name, prec in (("fp64", xs.PREC_FP64), ("fp32", xs.PREC_MIXED)):
+        mm = xs.EmissionModel(atm, prec=prec, device=dev, lines=lines, method="modit", n_gamma=16)
+        F = mm.forward(W.THETA_STAR).clone()
+        mm.set_observation(F * (1.0 + 0.01 * torch.as_tensor(W.std_normal(N), device=dev)), 0.01 * F)
+        t, _ = timed(lambda: mm.logl_grad_async(theta))
+        res[f"step_fwd_grad_{name}_ms"] = t
+        del mm
+        torch.cuda.empty_cache()
     d32 = torch.cat([((a - b).abs() / b.abs().amax(dim=1, keepdim=True)).flatten()
                      for a, b in zip(out["fp32"][1], out["fp64"][1])])
     res["fp32_vs_fp64_max_rel_to_layer_max"] = float(d32.max())
