@@ -359,3 +359,46 @@ def rotation(F0, nu, vsini, u1, u2):
 def ip_rv(F1, nu, nu_out, beta, rv):
     """Gaussian instrumental profile and radial velocity onto the output grid (Sec. 4.2, Eq. responsenu)."""
     return response(F1, nu, nu_out, lambda v: gauss_ip(v, beta), rv)
+
+
+# ------------------------------------------------------------------ weak-line pre-filter (App. G)
+
+
+def contribution_filter(lines, p_bar, dp_bar, T_scan, vmr, g=1e5, mu=2.313, kappa_coef=1e-8, margin=2, sb=1.0):
+    """Lines that can contribute to the emission (App. G).  Per line: the isothermal
+    temperature T* of the scan at which S(T) is largest (first on ties); at T*, the
+    line-centre layer optical depths dtau_n = (dP_n/g)(vmr/(mu m_u)) S/(sqrt(2 pi) beta)
+    erfcx(gamma_n/(sqrt2 beta)) (the optical-depth formula of the model applied to the
+    line-centre cross-section); the contribution psi_n = exp(-tau_n) dtau_n P_n/dP_n with
+    tau_n = sum_{k<=n} dtau_k; its argmax n_hat (first on ties).  The same for the grey
+    continuum (kappa_coef P cm^2/g).  Returns (keep, n_hat per line, n_hat of the
+    continuum), keep = n_hat <= n_hat_cont + margin (layer index grows with pressure)."""
+    from scipy.special import erfcx
+    p = np.asarray(p_bar, dtype=np.float64)
+    dp = np.asarray(dp_bar, dtype=np.float64)
+    L, n = p.size, lines.nu_hat.size
+    best_S = np.full(n, -np.inf)
+    best_T = np.zeros(n)
+    for T in T_scan:
+        S, _, _ = line_params(lines, T, 1.0, sb)
+        better = S > best_S
+        best_S = np.where(better, S, best_S)
+        best_T = np.where(better, T, best_T)
+    sig0 = np.empty((L, n))  # line-centre cross-section per layer at each line's T*
+    for T in np.unique(best_T):
+        idx = np.nonzero(best_T == T)[0]
+        sub = lines.subset(idx)
+        for k in range(L):
+            S, beta, gam = line_params(sub, T, p[k], sb)
+            sig0[k, idx] = S / (np.sqrt(2.0 * np.pi) * beta) * erfcx(gam / (np.sqrt(2.0) * beta))
+    dtau = tau([sig0], np.full((1, L), vmr), p, dp, g, mu, 0.0)
+    dtc = tau([np.zeros((L, 1))], np.zeros((1, L)), p, dp, g, mu, kappa_coef)[:, 0]
+
+    def nhat(dt):
+        t = np.cumsum(dt, axis=0)
+        psi = np.exp(-t) * dt * (p / dp).reshape((L,) + (1,) * (dt.ndim - 1))
+        return np.argmax(psi, axis=0)
+
+    nh = nhat(dtau)
+    nc = int(nhat(dtc))
+    return nh <= nc + margin, nh, nc
