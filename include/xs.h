@@ -359,6 +359,23 @@ int xs_model_vjp(const xs_model* model, const double* theta, const double* g_F0,
                  size_t workspace_bytes, xs_stream stream);
 
 /*
+ * Weak-line pre-filter (App. G).  For every line, at the temperature of T_scan
+ * (host [n_scan], n_scan <= 64) where its strength S(T) is largest, in an
+ * isothermal atmosphere with mixing ratio vmr: the line-centre layer optical
+ * depths dtau_n (the optical-depth formula of tau_layers applied to the
+ * line-centre cross-section S erfcx(gamma_n/(sqrt2 beta))/(sqrt(2 pi) beta)),
+ * the contribution function psi_n = exp(-tau_n) dtau_n P_n/dP_n with
+ * tau_n = sum_{k<=n} dtau_k, and its argmax n_hat (first on ties).  The grey
+ * continuum kappa_coef P [cm^2/g] gets its own n_hat; keep[l] = 1 when the
+ * line's n_hat <= the continuum's + margin (layer 0 at the top), else 0.
+ * keep [n] uint8 and n_hat [n] int32 (may be NULL) device outputs.
+ */
+int lines_contribution_filter(const xs_lines* lines, const double* P_bar, const double* dP_bar, int32_t L,
+                              const double* T_scan, int32_t n_scan, double vmr, double gravity, double mu,
+                              double kappa_coef, double broad_scale, int32_t margin, uint8_t* keep, int32_t* n_hat,
+                              xs_stream stream);
+
+/*
  * Diagnostics (no paper counterpart).  xs_profile(1) makes the library record a
  * CUDA event pair around every line-sum kernel launch (forward and adjoint,
  * on the launching stream) until xs_profile(0); xs_profile_read synchronises

@@ -92,6 +92,8 @@ def lib():
         L.response_workspace_bytes.argtypes = [i64]
         L.response_rotation_adjoint.argtypes = [vp, vp, vp, i64, d, d, d, vp, vp, vp, sz, vp]
         L.response_ip_rv_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, d, d, vp, vp, vp, sz, vp]
+        L.lines_contribution_filter.argtypes = [C.POINTER(XsLinesC), vp, vp, i32, C.POINTER(C.c_double), i32, d, d, d,
+                                                d, d, i32, vp, vp, vp]
         L.modit_adjoint_workspace_bytes.restype = sz
         L.modit_adjoint_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
         L.modit_compute_adjoint.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, vp,
@@ -135,6 +137,15 @@ class DeviceLines:
         self.q_exponent = float(lines.q_exponent)
         self.tensors = [torch.from_numpy(a).to(device) for a in arrs]
         self.nu_hat, self.ln_S0, self.elower, self.gamma_ref, self.n_temp = self.tensors
+
+    def select(self, mask):
+        """The lines where mask (bool device tensor [n]) is true, same order, on the device."""
+        out = DeviceLines.__new__(DeviceLines)
+        out.tensors = [t[mask].contiguous() for t in self.tensors]
+        out.n = out.tensors[0].numel()
+        out.mass_amu, out.q_exponent = self.mass_amu, self.q_exponent
+        out.nu_hat, out.ln_S0, out.elower, out.gamma_ref, out.n_temp = out.tensors
+        return out
 
     def struct(self):
         ptr = [t.data_ptr() if self.n else None for t in self.tensors]
@@ -244,6 +255,19 @@ def response_ip_rv_adjoint(g_F, F1, nu, nu_out, beta, rv=0.0, stream=None):
         _dev(g_F), _dev(F1), _dev(nu), nu.numel(), _dev(nu_out), nu_out.numel(), float(beta), float(rv), _dev(g_F1),
         _dev(g_rv), _dev(ws), ws.numel(), _stream(stream)))
     return g_F1, g_rv
+
+
+def contribution_filter(lines: DeviceLines, P_bar, dP_bar, T_scan, vmr, gravity=1e5, mu=2.313, kappa_coef=1e-8,
+                        broad_scale=1.0, margin=2, stream=None):
+    """Weak-line pre-filter of App. G: (keep bool [n], n_hat int32 [n]) on the device."""
+    keep = torch.zeros(max(lines.n, 1), dtype=torch.uint8, device=P_bar.device)
+    nh = torch.zeros(max(lines.n, 1), dtype=torch.int32, device=P_bar.device)
+    ts = (C.c_double * len(T_scan))(*[float(t) for t in T_scan])
+    s = lines.struct()
+    _check("lines_contribution_filter", lib().lines_contribution_filter(
+        C.byref(s), _dev(P_bar), _dev(dP_bar), P_bar.numel(), ts, len(T_scan), float(vmr), float(gravity), float(mu),
+        float(kappa_coef), float(broad_scale), int(margin), _dev(keep), _dev(nh), _stream(stream)))
+    return keep[:lines.n].bool(), nh[:lines.n]
 
 
 def modit_compute_adjoint(lines: DeviceLines, nu_min, nu_max, N, T, P_bar, g_sigma, broad_scale=1.0, n_gamma=16,
