@@ -54,6 +54,17 @@ def kernel_sources_sha256():
     return h.hexdigest()
 
 
+def job_throughput(ms_local, evals_per_step, steps, world, dist=None, device="cpu"):
+    """Whole-job time and throughput of `world` replicas: the slowest rank's time
+    (max over ranks) and the evaluations of all ranks over it."""
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, world * evals_per_step * steps / (t_max / 1000.0)
+
+
 def in_cut_triples(lines, nu, W_cut, L):
     c = np.sort(lines.nu_hat)
     lo = np.searchsorted(nu, c - W_cut, side="left")
@@ -399,13 +410,8 @@ def main():
     out = model.out.cpu().numpy()
     assert np.all(np.isfinite(out)), "non-finite logL or gradient"
 
-    t_max = ms
-    if world > 1:
-        tt = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
+    t_max, value = job_throughput(ms, evals_per_step, args.steps, world, dist, dev)
     ms_per_step = t_max / args.steps
-    value = world * evals_per_step * args.steps / (t_max / 1000.0)
 
     # end to end through the public API with host buffers: line lists, grid, layers
     # and the observed spectrum go host -> device every step; logL, gradient and the
