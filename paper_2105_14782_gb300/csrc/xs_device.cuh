@@ -52,16 +52,11 @@ template <> struct vec4<double> { using type = double4_32a; };
 // Per-precision Faddeeva tier table.
 template <class R> struct Tier;
 template <> struct Tier<float> {
-    static constexpr float z2_fast = 625.0f;   // |z| >= 25: line-sum fast form (K = 2, real, per-line coefficients)
-    static constexpr float z2_fast_adj = 625.0f; // |z| >= 25: adjoint fast form (K = 1; error < 6e-6 of a term)
-    static constexpr float z2_far = 625.0f;    // |z| >= 25 : K = 2
-    static constexpr float z2_mid1 = 100.0f;   // |z| >= 10 : K = 4
-    static constexpr float z2_mid2 = 42.25f;   // |z| >= 6.5: K = 6, below: series
-    static constexpr float z2_series = 64.0f;  // the line sum uses the series below |z| = 8 (K = 5 form above)
-    static constexpr int K1 = 2, K2 = 4, K3 = 6;
+    // The FP32 path evaluates w only through the wing forms (|z| >= 25, main
+    // kernels), the polynomial in 1/|z|^2 (6 <= |z| < 25) and the series below
+    // |z| = 6 (near kernels, w_series_tab); these are the series' parameters.
+    static constexpr float z2_series = 64.0f;  // K(a) is precomputed for lines with a^2 below this
     static constexpr float h = 0.7f;           // series step (error ~1e-8 relative)
-    static constexpr int nwin = 8;             // E_n^- kept for |n - x/h| <= nwin
-    static constexpr float tcut = 5.3f;        // E_n^+ kept while nh + x < tcut
 };
 template <> struct Tier<double> {
     static constexpr double z2_fast = 1e300;   // no truncated fast form in double precision
@@ -223,78 +218,6 @@ __device__ __forceinline__ void w_series(R xh, R xl, R a, R Kc, R* wr, R* wi)
     *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
 }
 
-// FP32 small-|z| series with the E_n^- taken by a two-way recurrence from the
-// term nearest the peak, n0 = round(x/h), where t = n0 h - x = delta is small:
-//   E_{n0+k} = E_{n0+k-1} e^{-2h delta} q^{2k-1},  E_{n0-k} = E_{n0-k+1} e^{+2h delta} q^{2k-1},
-//   q = e^{-h^2};
-// every factor has a small exponent, so no digits are lost to e^{-x^2} e^{2nhx}.
-// E_n^+ = E_n^- e^{-4nhx} rides along in the same loop.  Terms with |k| > 6 are
-// below 1e-9 of the peak term.  dtab[n-1] = 1/(n^2 h^2 + a^2) for n = 1..32
-// (one table per line, shared by the warp; nullptr: computed here).
-__device__ __forceinline__ void w_series_rec(float xh, float xl, float a, float Kc, const float* dtab, float* wr,
-                                             float* wi)
-{
-    const float h = Tier<float>::h;
-    const int nw = 6;
-    // q^(2k-1), q = exp(-h^2) with h = 0.7f
-    const float Q[6] = {0.61262643f, 0.22992550f, 0.08629359f, 0.03238694f, 0.012155180f, 0.0045619742f};
-    const float x = xh;
-    const float a2 = a * a;
-    const int n0 = __float2int_rn(x * (1.0f / h));
-    const float delta = fmaf((float)n0, h, -xh) - xl;
-    // small arguments (|delta| <= h/2): the fast exponential is within 2 ulp
-    const float E0 = __expf(-delta * delta);
-    const float P = __expf(-2.0f * h * delta);
-    const float Pi = __expf(2.0f * h * delta);
-    // powers of R = e^{-4hx} for the E_n^+ = E_n^- R^n; they matter only where
-    // 4hx is small (x < 1), elsewhere E_n^+ is negligible against E_n^-
-    const float R4 = __expf(-4.0f * h * x);
-    const float R4i = rcp_fast(R4);
-    float Rn = __expf(-4.0f * h * x * (float)n0);
-    auto dn = [&](int n) -> float {
-        if (dtab != nullptr && n <= 32) return dtab[n - 1];
-        float nh = (float)n * h;
-        return rcp_fast(fmaf(nh, nh, a2));
-    };
-    float sc = 0.0f, ss = 0.0f;
-    if (n0 >= 1) {
-        float d = dn(n0);
-        float ep = E0 * Rn;
-        sc = d * (E0 + ep);
-        ss = (float)n0 * h * d * (E0 - ep);
-    }
-    float Eu = E0, Ed = E0, Ru = Rn, Rd = Rn;
-#pragma unroll
-    for (int k = 1; k <= nw; ++k) {
-        Eu = Eu * P * Q[k - 1];
-        Ed = Ed * Pi * Q[k - 1];
-        Ru = Ru * R4;
-        Rd = Rd * R4i;
-        const int nu = n0 + k;
-        const float du = dn(nu);
-        const float epu = Eu * Ru;
-        sc = fmaf(du, Eu + epu, sc);
-        ss = fmaf((float)nu * h * du, Eu - epu, ss);
-        const int nd = n0 - k;
-        if (nd >= 1) {
-            const float dd = dn(nd);
-            const float epd = Ed * Rd;
-            sc = fmaf(dd, Ed + epd, sc);
-            ss = fmaf((float)nd * h * dd, Ed - epd, ss);
-        }
-    }
-    float ex = exp_negsq(xh) * (1.0f - 2.0f * xh * xl);
-    float sax, cax;
-    sincosf(a * x, &sax, &cax);
-    const float c2v = 1.0f - 2.0f * sax * sax; // cos 2ax
-    const float s2 = 2.0f * sax * cax;         // sin 2ax
-    float sax_a = (a > 0.0f) ? sax * rcp_fast(a) : x;
-    float s2_a = 2.0f * sax_a * cax;
-    const float hpi = h * (float)(1.0 / PI);
-    *wr = ex * (Kc * c2v + 2.0f * hpi * sax * sax_a) + a * hpi * sc;
-    *wi = ex * (-Kc * s2 + hpi * s2_a) + hpi * ss;
-}
-
 // Per-line table for w_series_tab (near kernels, |z| < 6 so n0 = round(x/h) <= 9):
 // d[n + SER_OFF] = 1/(n^2 h^2 + a^2) for n = 1 .. SER_TAB - 1 - SER_OFF, and 0 for
 // n <= 0 (terms that do not exist).
@@ -313,9 +236,15 @@ __device__ __forceinline__ void series_table(float a, float* d)
     }
 }
 
-// The series of w_series_rec with the line's table (series_table) and the
-// terms above and below the peak taken as packed pairs: the same terms at a
-// fraction of the instructions.  0 <= x < 6.3.
+// FP32 small-|z| series (near kernels, 0 <= x < 6.3) with the E_n^- taken by a
+// two-way recurrence from the term nearest the peak, n0 = round(x/h), where
+// t = n0 h - x = delta is small:
+//   E_{n0+k} = E_{n0+k-1} e^{-2h delta} q^{2k-1},  E_{n0-k} = E_{n0-k+1} e^{+2h delta} q^{2k-1},
+//   q = e^{-h^2};
+// every factor has a small exponent, so no digits are lost to e^{-x^2} e^{2nhx}.
+// E_n^+ = E_n^- e^{-4nhx} rides along.  Terms with |k| > 6 are below 1e-9 of the
+// peak term.  The terms above and below the peak go as packed pairs, with the
+// line's table of 1/(n^2 h^2 + a^2) (series_table).
 __device__ __forceinline__ void w_series_tab(float xh, float xl, float a, float Kc, const float* dt, float* wr,
                                              float* wi)
 {
@@ -367,14 +296,8 @@ __device__ __forceinline__ void w_small(R x, R xl, R a, R Kc, const R*, R* wr, R
 {
     w_series<R>(x, xl, a, Kc, wr, wi);
 }
-template <>
-__device__ __forceinline__ void w_small<float>(float x, float xl, float a, float Kc, const float* dtab, float* wr,
-                                               float* wi)
-{
-    w_series_rec(x, xl, a, Kc, dtab, wr, wi);
-}
 
-// w(x + ia) for any tier; x = x + xl >= 0; dtab: see w_series_rec (may be nullptr).
+// w(x + ia) for any tier (the FP64 path); x = x + xl >= 0; dtab is not used.
 template <class R>
 __device__ __forceinline__ void faddeeva(R x, R xl, R a, R Kc, R* wr, R* wi, const R* dtab = nullptr)
 {
