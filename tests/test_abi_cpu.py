@@ -69,3 +69,44 @@ def test_invalid_arguments_rejected_before_launch(lib):
     assert lib.emission_spectrum(None, None, None, 0, 5, None, None) == -1
     lib.layer_temperatures.argtypes = [C.c_double, C.c_double, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p]
     assert lib.layer_temperatures(-5.0, 0.1, None, 3, None, None) == -1
+
+
+def test_workspace_queries_of_the_other_entry_points(lib):
+    lib.modit_workspace_bytes.restype = C.c_size_t
+    lib.modit_workspace_bytes.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_int64, C.c_int]
+    lib.modit_adjoint_workspace_bytes.restype = C.c_size_t
+    lib.modit_adjoint_workspace_bytes.argtypes = lib.modit_workspace_bytes.argtypes
+    a = lib.modit_workspace_bytes(200_000, 100, 16, 65536, 0)
+    b = lib.modit_workspace_bytes(200_000, 100, 16, 65536, 1)
+    assert a > b > 0  # FP32 distribution and transforms take less
+    # distribution + transform + output rows at least
+    assert a >= 100 * 16 * 65536 * 8 + 100 * 16 * 32769 * 16
+    assert lib.modit_adjoint_workspace_bytes(200_000, 100, 16, 65536, 0) > a
+    assert lib.modit_workspace_bytes(10, 1, 16, 1000, 0) == 0   # not a power of two
+    assert lib.modit_workspace_bytes(10, 1, 33, 1024, 0) == 0   # too many gamma nodes
+    assert lib.modit_workspace_bytes(10, 0, 16, 1024, 0) == 0   # no layers
+    lib.response_workspace_bytes.restype = C.c_size_t
+    lib.response_workspace_bytes.argtypes = [C.c_int64]
+    assert lib.response_workspace_bytes(0) == 0
+    assert lib.response_workspace_bytes(1000) >= 1000 * 8
+
+
+def test_new_entry_points_reject_bad_arguments_before_launch(lib):
+    vp = C.c_void_p
+    lib.modit_compute.argtypes = [vp, C.c_double, C.c_double, C.c_int64, vp, vp, C.c_int32, C.c_double, C.c_int32,
+                                  C.c_int64, C.c_int, vp, vp, C.c_size_t, vp]
+    assert lib.modit_compute(None, 4340.0, 4390.0, 100, None, None, 1, 1.0, 16, 256, 0, None, None, 0, None) == -1
+    lib.response_rotation.argtypes = [vp, vp, C.c_int64, C.c_double, C.c_double, C.c_double, vp, vp]
+    assert lib.response_rotation(None, None, 10, 30.0, 0.4, 0.2, None, None) == -1
+    lib.response_ip_rv.argtypes = [vp, vp, C.c_int64, vp, C.c_int64, C.c_double, C.c_double, vp, vp]
+    assert lib.response_ip_rv(None, None, 10, None, 10, 2.0, 0.0, None, None) == -1
+    lib.lines_contribution_filter.argtypes = [vp, vp, vp, C.c_int32, vp, C.c_int32, C.c_double, C.c_double,
+                                              C.c_double, C.c_double, C.c_double, C.c_int32, vp, vp, vp]
+    assert lib.lines_contribution_filter(None, None, None, 10, None, 1, 1e-3, 1e5, 2.313, 0.1, 1.0, 2, None, None,
+                                         None) == -1
+    lib.xs_model_vjp.argtypes = [vp] * 7
+    assert lib.xs_model_vjp(None, None, None, None, None, None, None) == -1
+    lib.xs_model_forward_keep.argtypes = [vp] * 6
+    assert lib.xs_model_forward_keep(None, None, None, None, None, None) == -1
+    lib.xs_model_logl_grad_layers.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, C.c_size_t, vp]
+    assert lib.xs_model_logl_grad_layers(None, None, None, 1.0, None, None, None, 0, None) == -1
