@@ -8,9 +8,9 @@
 //      layer-independent parts of S(T) and ln gamma' (modit_prepass_kernel);
 //   2. the lineshape distribution S[k][j]: each line adds S(T) (Eq. Slog) to the
 //      two q nodes around q_l and the two ln gamma' nodes around its width, with
-//      linear weights (modit_lsd_kernel).  One thread per q node gathers the lines
-//      with q_l in [j-1, j+1) by binary search, so the sum has a fixed order (no
-//      atomics);
+//      linear weights (modit_lsd_kernel).  One thread per q node takes the lines
+//      with floor(q_l) = j (binary search) and hands the upper node's share to its
+//      neighbour through shared memory, so the sum has a fixed order (no atomics);
 //   3. batched real FFTs of the n_gamma rows (cuFFT);
 //   4. Y[f] = sum_k FT(S_k)[f] K_k[f], K_k = exp(-2 pi^2 beta'^2 f^2)
 //      (exp(-2 pi gamma'_k |f|) - gamma'_k DFT(A)[f]), beta' = R0 beta/nu_hat (common
@@ -32,7 +32,7 @@
 namespace xsd {
 
 constexpr int MODIT_MAX_GAMMA = 32;
-constexpr int MODIT_THREADS = 256;
+constexpr int MODIT_THREADS = 128;
 
 template <class R> struct CplxOf;
 template <> struct CplxOf<double> { using type = cufftDoubleComplex; };
@@ -97,11 +97,13 @@ __device__ __forceinline__ int64_t first_at_least(const double* v, int64_t n, do
     return lo;
 }
 
-// One thread per (layer, slot): node j = slot, or slot - M for the left padding.
-// Lines with floor(q_l) == j give weight 1 - w, those with floor(q_l) == j - 1
-// give w (w = q_l - floor(q_l)); they are found by binary search on the
-// (monotone) q_l of the prepass.  Per line and layer: S(T) (Eq. Slog) from one
-// exp and one expm1, ln gamma' from the prepass by FMAs.
+// One thread per (layer, slot); node j = slot, or slot - M for the left padding.
+// Each thread takes the lines with floor(q_l) == j (found by binary search on
+// the monotone q_l of the prepass), so every line is visited once: weight 1 - w
+// goes to node j, w to node j + 1 through shared memory (the slot before the
+// block's first comes from an extra halo thread).  Per line and layer: S(T)
+// (Eq. Slog) from one exp and one expm1, ln gamma' from the prepass by FMAs.
+// Blocks of MODIT_THREADS threads write MODIT_THREADS - 1 slots.
 template <class R>
 __global__ void __launch_bounds__(MODIT_THREADS) modit_lsd_kernel(
     const double* __restrict__ nu_hat, const double* __restrict__ ln_S0, const double* __restrict__ elower,
@@ -110,48 +112,54 @@ __global__ void __launch_bounds__(MODIT_THREADS) modit_lsd_kernel(
     const double* __restrict__ P, double sb, double scale, int64_t N, int64_t M, int ng,
     const unsigned long long* __restrict__ range, R* __restrict__ lsd)
 {
-    const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ double shR[MODIT_THREADS][MODIT_MAX_GAMMA];
+    const int t = threadIdx.x;
     const int n = blockIdx.y;
-    if (s >= M) return;
+    const int64_t s_raw = (int64_t)blockIdx.x * (MODIT_THREADS - 1) + t - 1;
+    const bool valid = s_raw < M;
+    const int64_t s = (s_raw + M) % M; // the halo of block 0 is slot M - 1
     const int64_t j = (s < (M + N) / 2) ? s : s - M;
-    const double Tn = T[n];
-    const double lnTr = log(Tn / Tref);
-    const double bT = 1.0 / Tn - 1.0 / Tref;
-    const double lgP = log(sb * P[n] / bar_per_atm);
-    const double gmin = __longlong_as_double((long long)range[2 * n]);
-    const double gmax = __longlong_as_double((long long)range[2 * n + 1]);
-    const double lg0 = log(gmin);
-    const double dlg = (ng >= 2 && gmax > gmin) ? (log(gmax) - lg0) / (double)(ng - 1) : 0.0;
-    const double idlg = dlg > 0.0 ? 1.0 / dlg : 0.0;
-    double acc[MODIT_MAX_GAMMA];
-#pragma unroll
-    for (int k = 0; k < MODIT_MAX_GAMMA; ++k) acc[k] = 0.0;
-    const int64_t b = first_at_least(qv, nl, (double)(j - 1));
-    const int64_t e = first_at_least(qv, nl, (double)(j + 1));
-    for (int64_t l = b; l < e; ++l) {
-        const double q = qv[l];
-        const double fq = floor(q);
-        double wq;
-        if (fq == (double)j) wq = 1.0 - (q - fq);
-        else if (fq == (double)(j - 1)) wq = q - fq;
-        else continue;
-        const double S = exp(ln_S0[l] - c2 * elower[l] * bT - qexp * lnTr) *
-                         (expm1(-c2 * nu_hat[l] / Tn) / sden[l]) * scale;
-        int k0 = 0;
-        double wk = 0.0;
-        if (dlg > 0.0) {
-            const double t = (lgref[l] + lgP - n_temp[l] * lnTr - lg0) * idlg;
-            k0 = min(max((int)floor(t), 0), ng - 2);
-            wk = t - (double)k0;
-        }
-        const double v = S * wq;
-#pragma unroll
-        for (int k = 0; k < MODIT_MAX_GAMMA; ++k) {
-            if (k == k0) acc[k] += v * (1.0 - wk);
-            if (k == k0 + 1) acc[k] += v * wk;
+    double accL[MODIT_MAX_GAMMA], accR[MODIT_MAX_GAMMA];
+    for (int k = 0; k < ng; ++k) {
+        accL[k] = 0.0;
+        accR[k] = 0.0;
+    }
+    if (valid) {
+        const double Tn = T[n];
+        const double lnTr = log(Tn / Tref);
+        const double bT = 1.0 / Tn - 1.0 / Tref;
+        const double lgP = log(sb * P[n] / bar_per_atm);
+        const double gmin = __longlong_as_double((long long)range[2 * n]);
+        const double gmax = __longlong_as_double((long long)range[2 * n + 1]);
+        const double lg0 = log(gmin);
+        const double dlg = (ng >= 2 && gmax > gmin) ? (log(gmax) - lg0) / (double)(ng - 1) : 0.0;
+        const double idlg = dlg > 0.0 ? 1.0 / dlg : 0.0;
+        const int64_t b = first_at_least(qv, nl, (double)j);
+        const int64_t e = first_at_least(qv, nl, (double)(j + 1));
+        for (int64_t l = b; l < e; ++l) {
+            const double wq = qv[l] - (double)j;
+            const double S = exp(ln_S0[l] - c2 * elower[l] * bT - qexp * lnTr) *
+                             (expm1(-c2 * nu_hat[l] / Tn) / sden[l]) * scale;
+            int k0 = 0;
+            double wk = 0.0;
+            if (dlg > 0.0) {
+                const double tt = (lgref[l] + lgP - n_temp[l] * lnTr - lg0) * idlg;
+                k0 = min(max((int)floor(tt), 0), ng - 2);
+                wk = tt - (double)k0;
+            }
+            const double vl = S * (1.0 - wq), vr = S * wq;
+            accL[k0] += vl * (1.0 - wk);
+            accR[k0] += vr * (1.0 - wk);
+            if (dlg > 0.0) {
+                accL[k0 + 1] += vl * wk;
+                accR[k0 + 1] += vr * wk;
+            }
         }
     }
-    for (int k = 0; k < ng; ++k) lsd[((size_t)n * ng + k) * M + s] = (R)acc[k];
+    for (int k = 0; k < ng; ++k) shR[t][k] = accR[k];
+    __syncthreads();
+    if (t >= 1 && valid)
+        for (int k = 0; k < ng; ++k) lsd[((size_t)n * ng + k) * M + s] = (R)(accL[k] + shR[t - 1][k]);
 }
 
 // A(d) = sum over p != 0 of 1/(pi (d + pM)^2) on one period (index d mod M):
@@ -383,12 +391,13 @@ __global__ void modit_adj_line_term(const double* __restrict__ nu_hat, const dou
             dt = (-n_temp[l] / Tn - dlg0 - t * ddlg) / dlg;
         }
         const int k1 = (dlg > 0.0) ? k0 + 1 : 0;
-        const int64_t jlo = -(M - N) / 2, jhi = (M + N) / 2; // nodes gathered by the forward
+        // the forward gathers lines whose lower node j0 lies in the window
+        // -(M-N)/2 .. (M+N)/2 - 1 and adds to the slots of j0 and j0 + 1 (mod M)
+        const int64_t jlo = -(M - N) / 2, jhi = (M + N) / 2;
         double A = 0.0, B = 0.0;
         for (int d = 0; d < 2; ++d) {
-            const int64_t j = j0 + d;
-            if (j < jlo || j >= jhi) continue;
-            const int64_t sl = ((j % M) + M) % M;
+            if (j0 < jlo || j0 >= jhi) break;
+            const int64_t sl = (((j0 + d) % M) + M) % M;
             const double w = d ? wq : 1.0 - wq;
             const double c0 = (double)corr[((size_t)n * ng + k0) * M + sl];
             const double c1 = (double)corr[((size_t)n * ng + k1) * M + sl];
@@ -560,7 +569,7 @@ int run_modit(const xs_lines* ln, double nu_min, double nu_max, int64_t N, const
     double* lgref = sden + nl;
     modit_prepass_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, ln->gamma_ref, nl, nu_min, R0, qv,
                                                                         sden, lgref);
-    modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 1) / MODIT_THREADS), (unsigned)L), MODIT_THREADS, 0,
+    modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 2) / (MODIT_THREADS - 1)), (unsigned)L), MODIT_THREADS, 0,
                           st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->n_temp, qv, sden, lgref, nl, ln->q_exponent,
                                 T, P, sb, scale, N, M, ng, range, lsd);
     modit_images_kernel<R><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, A);
@@ -620,7 +629,7 @@ int run_modit_adjoint(const xs_lines* ln, double nu_min, double nu_max, int64_t 
     double* lgref = sden + nl;
     modit_prepass_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(ln->nu_hat, ln->gamma_ref, nl, nu_min, R0, qv,
                                                                         sden, lgref);
-    modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 1) / MODIT_THREADS), (unsigned)L), MODIT_THREADS, 0,
+    modit_lsd_kernel<R><<<dim3((unsigned)((M + MODIT_THREADS - 2) / (MODIT_THREADS - 1)), (unsigned)L), MODIT_THREADS, 0,
                           st>>>(ln->nu_hat, ln->ln_S0, ln->elower, ln->n_temp, qv, sden, lgref, nl, ln->q_exponent,
                                 T, P, sb, scale, N, M, ng, range, lsd);
     modit_images_kernel<R><<<(unsigned)((M + 255) / 256), 256, 0, st>>>(M, A);
