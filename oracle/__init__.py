@@ -49,6 +49,7 @@ def _load():
             lib.orc_xs_points.argtypes = [_i64, _pd, _pd, _pd, _pd, _pd, _d, _d, _pd, _i32, _pd, _pd, _d, _d,
                                           _i64, C.POINTER(C.c_int32), C.POINTER(C.c_int64), _pd]
             lib.orc_tau.argtypes = [_i32, C.POINTER(_pd), _pd, _pd, _pd, _i32, _i64, _d, _d, _d, _pd]
+            lib.orc_tau_cia.argtypes = [_pd, _pd, _i32, _pd, _pd, _pd, _i32, _i64, _d, _d, _d, _d, _pd]
             for f in ("orc_e1", "orc_e2", "orc_e3", "orc_trans"):
                 getattr(lib, f).argtypes = [_d]
                 getattr(lib, f).restype = _d
@@ -135,6 +136,18 @@ def tau(sigmas, vmr, P_bar, dP_bar, g=1e5, mu=2.313, kappa_coef=1e-8):
     ptrs = (_pd * len(sig))(*[_p(s) for s in sig])
     out = np.empty((L, N))
     _load().orc_tau(len(sig), ptrs, _p(vm), _p(P), _p(dP), L, N, g, mu, kappa_coef, _p(out))
+    return out
+
+
+def tau_cia(alpha, T_grid, T, P_bar, dP_bar, vmr1, vmr2, g=1e5, mu=2.313):
+    """dtau[L][N] of a collision-induced absorption pair (Sec. 2.4, Eq. taucont) from the
+    table alpha[nT][N] (cm^5) on the model grid, linear in T between T_grid (clamped)."""
+    alpha = _f64(alpha)
+    Tg, T, P, dP = _f64(T_grid), _f64(np.atleast_1d(T)), _f64(P_bar), _f64(dP_bar)
+    nT, N = alpha.shape
+    out = np.empty((T.size, N))
+    _load().orc_tau_cia(_p(alpha), _p(Tg), nT, _p(T), _p(P), _p(dP), T.size, N, float(vmr1), float(vmr2),
+                        float(g), float(mu), _p(out))
     return out
 
 

@@ -292,6 +292,40 @@ void orc_xs_points(int64_t nl, const double* nu_hat, const double* lnS0, const d
 /* column factor dP/(mu m_u g) in molecules per cm^2 for a pressure step in bar */
 static double column(double dP_bar, double mu, double g) { return dP_bar * 1e6 / (mu * o_mu * g); }
 
+/* Collision-induced absorption (Sec. 2.4, Eq. taucont): for each layer and grid
+ * point, dtau = n1 n2 alpha(T, nu) H dP/P with n_i = vmr_i P / (kB T) and the
+ * scale height H = kB T / (mu m_u g); alpha interpolated linearly in T between the
+ * table's temperatures (clamped at its ends), per grid point.  alpha [nT][N],
+ * Tgrid [nT] increasing; dtau [L][N] written. */
+void orc_tau_cia(const double* alpha, const double* Tgrid, int32_t nT, const double* T, const double* P_bar,
+                 const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2, double g, double mu,
+                 double* dtau)
+{
+    for (int32_t n = 0; n < L; ++n) {
+        const double Tn = T[n];
+        int32_t k = 0;
+        double w = 0.0;
+        if (Tn <= Tgrid[0]) {
+            k = 0;
+            w = 0.0;
+        } else if (Tn >= Tgrid[nT - 1]) {
+            k = nT - 2 < 0 ? 0 : nT - 2;
+            w = nT > 1 ? 1.0 : 0.0;
+        } else {
+            while (k + 1 < nT - 1 && Tgrid[k + 1] <= Tn) ++k;
+            w = (Tn - Tgrid[k]) / (Tgrid[k + 1] - Tgrid[k]);
+        }
+        const double P = P_bar[n] * 1e6, dP = dP_bar[n] * 1e6;
+        const double n1 = vmr1 * P / (o_kB * Tn), n2 = vmr2 * P / (o_kB * Tn);
+        const double H = o_kB * Tn / (mu * o_mu * g);
+        for (int64_t j = 0; j < N; ++j) {
+            const double a0 = alpha[(size_t)k * N + j];
+            const double a = (nT > 1) ? a0 + w * (alpha[(size_t)(k + 1) * N + j] - a0) : a0;
+            dtau[(size_t)n * N + j] = n1 * n2 * a * H * dP / P;
+        }
+    }
+}
+
 /* sigma_all: S species, each [L][N]; vmr [S][L]. */
 void orc_tau(int32_t S, const double* const* sigma, const double* vmr, const double* P_bar,
              const double* dP_bar, int32_t L, int64_t N, double g, double mu, double kappa_coef,

@@ -169,3 +169,16 @@ def serving_requests(n: int, seed: int = SEED_SERVE):
     ng = rng.integers(2000, 50001, n)
     nlay = rng.integers(20, 201, n)
     return nl, ng, nlay
+
+
+def cia_table(nu, T_grid=None, alpha0=1e-46, seed=SEED_THETA + 10):
+    """A smooth synthetic collision-induced absorption table alpha[nT][N] (cm^5)
+    on the grid nu, standing in for a HITRAN CIA table: a broad band centred near
+    the middle of the grid whose strength grows with temperature."""
+    rng = np.random.default_rng(seed)
+    T_grid = np.arange(400.0, 3001.0, 200.0) if T_grid is None else np.asarray(T_grid, dtype=np.float64)
+    nu = np.asarray(nu, dtype=np.float64)
+    c = 0.5 * (nu[0] + nu[-1]) + rng.uniform(-1.0, 1.0)
+    width = 4.0 * (nu[-1] - nu[0]) + 1.0
+    band = np.exp(-((nu - c) / width) ** 2)
+    return T_grid, alpha0 * (T_grid[:, None] / 1000.0) ** 0.8 * band[None, :]
