@@ -181,6 +181,23 @@ int tau_layers_adjoint(const void* const* sigma, int32_t S, const double* vmr, c
 int emission_spectrum(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
                       xs_stream stream);
 
+/*
+ * Collision-induced absorption of one molecule pair (Sec. 2.4, Eq. taucont):
+ *   dtau[n][j] (+)= n1 n2 alpha(T_n, nu_j) H dP_n/P_n,  n_i = vmr_i P/(kB T),
+ *   H = kB T/(mu m_u g) (Eq. scaleheight),
+ * alpha from the table alpha [nT][N] (cm^5, on the model grid) at the temperatures
+ * T_grid [nT] (increasing), linear in T and clamped at the ends (the paper
+ * interpolates in T only).  T, P_bar, dP_bar [L]; all device.  accumulate = 1 adds
+ * to dtau, 0 overwrites.  The adjoint adds to g_T [L] the derivative of
+ * sum g_dtau dtau in each T_n (fixed-order sums).
+ */
+int tau_cia(const double* alpha, const double* T_grid, int32_t nT, const double* T, const double* P_bar,
+            const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2, double gravity, double mu,
+            int accumulate, double* dtau, xs_stream stream);
+int tau_cia_adjoint(const double* g_dtau, const double* alpha, const double* T_grid, int32_t nT, const double* T,
+                    const double* P_bar, const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2,
+                    double gravity, double mu, double* g_T, xs_stream stream);
+
 /* Workspace bytes emission_spectrum_adjoint needs. */
 size_t emission_workspace_bytes(int32_t L, int64_t N);
 
@@ -234,6 +251,13 @@ typedef struct {
     int32_t n_gamma;
     double nu_min, nu_max;
     int64_t n_fft[XS_MAX_SPECIES];
+    /* Optional collision-induced absorption (tau_cia) added to the optical depth:
+     * table cia_alpha [cia_nT][N] and cia_T [cia_nT] (device), pair mixing ratios;
+     * unused when cia_alpha is NULL. */
+    const double* cia_alpha;
+    const double* cia_T;
+    int32_t cia_nT;
+    double cia_vmr1, cia_vmr2;
 } xs_model;
 
 enum { XS_METHOD_LPF = 0, XS_METHOD_MODIT = 1 };

@@ -219,6 +219,27 @@ int emission_spectrum(const double* dtau, const double* T, const double* nu, int
     return xsi::rt_emission(dtau, T, nu, L, N, F0, S(stream));
 }
 
+int tau_cia(const double* alpha, const double* T_grid, int32_t nT, const double* T, const double* P_bar,
+            const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2, double gravity, double mu,
+            int accumulate, double* dtau, xs_stream stream)
+{
+    if (!alpha || !T_grid || nT < 1 || !T || !P_bar || !dP_bar || L <= 0 || N <= 0 || !dtau) return XS_EINVAL;
+    if (!(gravity > 0.0) || !(mu > 0.0) || !(vmr1 >= 0.0) || !(vmr2 >= 0.0)) return XS_EINVAL;
+    return xsi::rt_tau_cia(alpha, T_grid, nT, T, P_bar, dP_bar, L, N, vmr1, vmr2, gravity, mu, accumulate != 0, dtau,
+                           S(stream));
+}
+
+int tau_cia_adjoint(const double* g_dtau, const double* alpha, const double* T_grid, int32_t nT, const double* T,
+                    const double* P_bar, const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2,
+                    double gravity, double mu, double* g_T, xs_stream stream)
+{
+    if (!g_dtau || !alpha || !T_grid || nT < 1 || !T || !P_bar || !dP_bar || L <= 0 || N <= 0 || !g_T)
+        return XS_EINVAL;
+    if (!(gravity > 0.0) || !(mu > 0.0)) return XS_EINVAL;
+    return xsi::rt_tau_cia_adjoint(g_dtau, alpha, T_grid, nT, T, P_bar, dP_bar, L, N, vmr1, vmr2, gravity, mu, g_T,
+                                   S(stream));
+}
+
 size_t emission_workspace_bytes(int32_t L, int64_t N)
 {
     if (L <= 0 || N <= 0) return 0;
@@ -268,6 +289,8 @@ int check_model(const xs_model* m)
     for (int s = 0; s < m->n_species; ++s)
         if (check_lines(&m->species[s])) return XS_EINVAL;
     if (m->method != XS_METHOD_LPF && m->method != XS_METHOD_MODIT) return XS_EINVAL;
+    if (m->cia_alpha && (!m->cia_T || m->cia_nT < 1 || !(m->cia_vmr1 >= 0.0) || !(m->cia_vmr2 >= 0.0)))
+        return XS_EINVAL;
     if (m->method == XS_METHOD_MODIT) {
         if (m->n_gamma < 1 || m->n_gamma > 32 || !(m->nu_min > 0.0) || !(m->nu_max > m->nu_min) || m->N < 2)
             return XS_EINVAL;
@@ -360,6 +383,11 @@ int model_forward_impl(const xs_model* m, const double* theta, double* F0out, ch
     }
     r = xsi::rt_tau(sp, Sp, vmr, m->P_bar, m->dP_bar, m->L, m->N, m->gravity, m->mu, m->kappa_coef, m->prec, dtau, st);
     if (r) return r;
+    if (m->cia_alpha) {
+        r = xsi::rt_tau_cia(m->cia_alpha, m->cia_T, m->cia_nT, T, m->P_bar, m->dP_bar, m->L, m->N, m->cia_vmr1,
+                            m->cia_vmr2, m->gravity, m->mu, 1, dtau, st);
+        if (r) return r;
+    }
     return xsi::rt_emission(dtau, T, m->nu, m->L, m->N, F0out, st);
 }
 
@@ -409,6 +437,10 @@ int model_adjoint_impl(const xs_model* m, const double* theta, const double* gF,
     double* gb = (double*)(ws + p.gb);
     int r;
     if ((r = xsi::rt_emission_adjoint(gF, dtau, T, m->nu, m->L, m->N, gdtau, gT, ws + p.emws, st))) return r;
+    if (m->cia_alpha &&
+        (r = xsi::rt_tau_cia_adjoint(gdtau, m->cia_alpha, m->cia_T, m->cia_nT, T, m->P_bar, m->dP_bar, m->L, m->N,
+                                     m->cia_vmr1, m->cia_vmr2, m->gravity, m->mu, gT, st)))
+        return r;
     const void* sp[XS_MAX_SPECIES];
     double* gsp[XS_MAX_SPECIES];
     for (int s = 0; s < Sp; ++s) {

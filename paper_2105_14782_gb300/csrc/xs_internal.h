@@ -44,6 +44,12 @@ int rt_fill_vmr(const double* theta_dev_unused, int32_t S, int32_t L, const doub
 int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* log10_vmr_host, double sb,
                   const double* T, const double* P, const double* g_T, const double* g_vmr, const double* g_b,
                   double* out, cudaStream_t st);
+int rt_tau_cia(const double* alpha, const double* Tg, int32_t nT, const double* T, const double* P, const double* dP,
+               int32_t L, int64_t N, double vmr1, double vmr2, double g, double mu, int accumulate, double* dtau,
+               cudaStream_t st);
+int rt_tau_cia_adjoint(const double* g_dtau, const double* alpha, const double* Tg, int32_t nT, const double* T,
+                       const double* P, const double* dP, int32_t L, int64_t N, double vmr1, double vmr2, double g,
+                       double mu, double* g_T, cudaStream_t st);
 int rt_layer_grad(int32_t S, int32_t L, const double* log10_vmr_host, const double* g_T, const double* g_vmr,
                   const double* g_b, double* out, cudaStream_t st);
 int rt_accumulate(double* dst, const double* src, int64_t n, int first, cudaStream_t st);

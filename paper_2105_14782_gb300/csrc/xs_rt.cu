@@ -318,6 +318,81 @@ __global__ void theta_grad_kernel(int S, int L, double T0, VmrArgs a, const doub
     out[3 + S] = gb;
 }
 
+// Collision-induced absorption (Sec. 2.4, Eq. taucont): dtau += n1 n2 alpha(T, nu) H dP/P,
+// n_i = vmr_i P/(kB T), H = kB T/(mu m_u g), alpha linear in T between the table's
+// temperatures (clamped).  = vmr1 vmr2 P dP alpha/(kB T mu m_u g) with P, dP in dyn/cm^2.
+__device__ __forceinline__ void cia_interp(const double* Tg, int nT, double T, int* k, double* w, double* dw)
+{
+    if (nT < 2 || T <= Tg[0]) {
+        *k = 0;
+        *w = 0.0;
+        *dw = 0.0;
+        return;
+    }
+    if (T >= Tg[nT - 1]) {
+        *k = nT - 2;
+        *w = 1.0;
+        *dw = 0.0;
+        return;
+    }
+    int lo = 0, hi = nT - 1; // Tg[lo] <= T < Tg[hi]
+    while (hi - lo > 1) {
+        const int m = (lo + hi) >> 1;
+        if (Tg[m] <= T) lo = m; else hi = m;
+    }
+    *k = lo;
+    *dw = 1.0 / (Tg[lo + 1] - Tg[lo]);
+    *w = (T - Tg[lo]) * *dw;
+}
+
+__global__ void tau_cia_kernel(const double* __restrict__ alpha, const double* __restrict__ Tg, int nT,
+                               const double* __restrict__ T, const double* __restrict__ P,
+                               const double* __restrict__ dP, int L, int64_t N, double c12, int accumulate,
+                               double* __restrict__ dtau)
+{
+    const int n = blockIdx.y;
+    int k;
+    double w, dw;
+    cia_interp(Tg, nT, T[n], &k, &w, &dw);
+    const double f = c12 * P[n] * dP[n] / T[n];
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < N; j += (int64_t)gridDim.x * blockDim.x) {
+        const double a0 = alpha[(size_t)k * N + j];
+        const double a = (nT > 1) ? a0 + w * (alpha[(size_t)(k + 1) * N + j] - a0) : a0;
+        const size_t i = (size_t)n * N + j;
+        dtau[i] = (accumulate ? dtau[i] : 0.0) + f * a;
+    }
+}
+
+// g_T[n] += sum_j g_dtau[n][j] d dtau[n][j]/dT_n, d/dT of f(T) alpha(T) with f ~ 1/T
+// (one block per layer, fixed-order sum)
+__global__ void tau_cia_adjoint_kernel(const double* __restrict__ g_dtau, const double* __restrict__ alpha,
+                                       const double* __restrict__ Tg, int nT, const double* __restrict__ T,
+                                       const double* __restrict__ P, const double* __restrict__ dP, int64_t N,
+                                       double c12, double* __restrict__ g_T)
+{
+    __shared__ double red[RT_THREADS];
+    const int n = blockIdx.x;
+    int k;
+    double w, dw;
+    cia_interp(Tg, nT, T[n], &k, &w, &dw);
+    const double f = c12 * P[n] * dP[n] / T[n];
+    double s = 0.0;
+    for (int64_t j = threadIdx.x; j < N; j += blockDim.x) {
+        const double a0 = alpha[(size_t)k * N + j];
+        const double a1 = (nT > 1) ? alpha[(size_t)(k + 1) * N + j] : a0;
+        const double a = a0 + w * (a1 - a0);
+        const double da = (a1 - a0) * dw;
+        s += g_dtau[(size_t)n * N + j] * f * (da - a / T[n]);
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) g_T[n] += red[0];
+}
+
 // Gradient for per-layer temperatures: out[1 + n] = dlogL/dT_n, then
 // dlogL/dlog10 vmr_m and dlogL/ds_b (out[0], logL, is left as it is).
 __global__ void layer_grad_kernel(int S, int L, VmrArgs a, const double* __restrict__ g_T,
@@ -448,6 +523,30 @@ int rt_theta_grad(int32_t S, int32_t L, double T0, double alpha, const double* l
     VmrArgs a{};
     for (int m = 0; m < S; ++m) a.lg[m] = lg[m];
     theta_grad_kernel<<<1, 32, 0, st>>>(S, L, T0, a, T, P, g_T, g_vmr, g_b, out);
+    return launched(1);
+}
+
+static double cia_c12(double vmr1, double vmr2, double g, double mu)
+{
+    return vmr1 * vmr2 * 1e12 / (kB * mu * amu * g); // P dP in bar^2 -> (dyn/cm^2)^2
+}
+
+int rt_tau_cia(const double* alpha, const double* Tg, int32_t nT, const double* T, const double* P, const double* dP,
+               int32_t L, int64_t N, double vmr1, double vmr2, double g, double mu, int accumulate, double* dtau,
+               cudaStream_t st)
+{
+    const unsigned gx = (unsigned)std::min<int64_t>((N + RT_THREADS - 1) / RT_THREADS, 1024);
+    tau_cia_kernel<<<dim3(gx, (unsigned)L), RT_THREADS, 0, st>>>(alpha, Tg, nT, T, P, dP, L, N,
+                                                                 cia_c12(vmr1, vmr2, g, mu), accumulate, dtau);
+    return launched(1);
+}
+
+int rt_tau_cia_adjoint(const double* g_dtau, const double* alpha, const double* Tg, int32_t nT, const double* T,
+                       const double* P, const double* dP, int32_t L, int64_t N, double vmr1, double vmr2, double g,
+                       double mu, double* g_T, cudaStream_t st)
+{
+    tau_cia_adjoint_kernel<<<L, RT_THREADS, 0, st>>>(g_dtau, alpha, Tg, nT, T, P, dP, N, cia_c12(vmr1, vmr2, g, mu),
+                                                     g_T);
     return launched(1);
 }
 

@@ -42,7 +42,8 @@ class XsModelC(C.Structure):
                 ("wing_cut", C.c_double), ("gravity", C.c_double), ("mu", C.c_double), ("kappa_coef", C.c_double),
                 ("d_obs", C.c_void_p), ("sig_obs", C.c_void_p), ("prec", C.c_int), ("method", C.c_int),
                 ("n_gamma", C.c_int32), ("nu_min", C.c_double), ("nu_max", C.c_double),
-                ("n_fft", C.c_int64 * MAX_SPECIES)]
+                ("n_fft", C.c_int64 * MAX_SPECIES), ("cia_alpha", C.c_void_p), ("cia_T", C.c_void_p),
+                ("cia_nT", C.c_int32), ("cia_vmr1", C.c_double), ("cia_vmr2", C.c_double)]
 
 
 def lib():
@@ -92,6 +93,8 @@ def lib():
         L.response_workspace_bytes.argtypes = [i64]
         L.response_rotation_adjoint.argtypes = [vp, vp, vp, i64, d, d, d, vp, vp, vp, sz, vp]
         L.response_ip_rv_adjoint.argtypes = [vp, vp, vp, i64, vp, i64, d, d, vp, vp, vp, sz, vp]
+        L.tau_cia.argtypes = [vp, vp, i32, vp, vp, vp, i32, i64, d, d, d, d, i, vp, vp]
+        L.tau_cia_adjoint.argtypes = [vp, vp, vp, i32, vp, vp, vp, i32, i64, d, d, d, d, vp, vp]
         L.lines_contribution_filter.argtypes = [C.POINTER(XsLinesC), vp, vp, i32, C.POINTER(C.c_double), i32, d, d, d,
                                                 d, d, i32, vp, vp, vp]
         L.modit_adjoint_workspace_bytes.restype = sz
@@ -257,6 +260,25 @@ def response_ip_rv_adjoint(g_F, F1, nu, nu_out, beta, rv=0.0, stream=None):
     return g_F1, g_rv
 
 
+def tau_cia(alpha, T_grid, T, P_bar, dP_bar, vmr1, vmr2, gravity=1e5, mu=2.313, out=None, stream=None):
+    """Collision-induced absorption optical depth [L][N] (Sec. 2.4); added to out when given."""
+    L, N = T.numel(), alpha.shape[1]
+    acc = out is not None
+    out = torch.empty((L, N), dtype=torch.float64, device=T.device) if out is None else out
+    _check("tau_cia", lib().tau_cia(_dev(alpha), _dev(T_grid), T_grid.numel(), _dev(T), _dev(P_bar), _dev(dP_bar), L,
+                                    N, float(vmr1), float(vmr2), float(gravity), float(mu), int(acc), _dev(out),
+                                    _stream(stream)))
+    return out
+
+
+def tau_cia_adjoint(g_dtau, alpha, T_grid, T, P_bar, dP_bar, vmr1, vmr2, gravity=1e5, mu=2.313, stream=None):
+    g_T = torch.zeros(T.numel(), dtype=torch.float64, device=T.device)
+    _check("tau_cia_adjoint", lib().tau_cia_adjoint(
+        _dev(g_dtau), _dev(alpha), _dev(T_grid), T_grid.numel(), _dev(T), _dev(P_bar), _dev(dP_bar), T.numel(),
+        alpha.shape[1], float(vmr1), float(vmr2), float(gravity), float(mu), _dev(g_T), _stream(stream)))
+    return g_T
+
+
 def contribution_filter(lines: DeviceLines, P_bar, dP_bar, T_scan, vmr, gravity=1e5, mu=2.313, kappa_coef=1e-8,
                         broad_scale=1.0, margin=2, stream=None):
     """Weak-line pre-filter of App. G: (keep bool [n], n_hat int32 [n]) on the device."""
@@ -367,8 +389,16 @@ class EmissionModel:
     calls of libxs.  theta = (T0, alpha, log10 vmr_0..log10 vmr_{S-1}, s_b)."""
 
     def __init__(self, atm, prec=PREC_MIXED, device="cuda", d_obs=None, sig_obs=None, lines=None, method="lpf",
-                 n_gamma=16):
+                 n_gamma=16, cia=None):
+        """cia: optional (T_grid [nT], alpha [nT][N], vmr1, vmr2), a collision-induced
+        absorption pair added to the optical depth (Sec. 2.4)."""
         self.device = torch.device(device)
+        self.cia = None
+        if cia is not None:
+            Tg, alpha, v1, v2 = cia
+            f64_ = dict(dtype=torch.float64, device=self.device)
+            self.cia = (torch.as_tensor(np.asarray(Tg), **f64_).contiguous(),
+                        torch.as_tensor(np.asarray(alpha), **f64_).contiguous(), float(v1), float(v2))
         self.prec = prec
         self.method, self.n_gamma = method, int(n_gamma)
         if method == "modit":
@@ -403,6 +433,9 @@ class EmissionModel:
             c.method, c.n_gamma, c.nu_min, c.nu_max = 1, self.n_gamma, nu0, nu1
             for i, sp_ in enumerate(self.species):
                 c.n_fft[i] = modit_fft_length(nu0, nu1, self.N, sp_)
+        if self.cia is not None:
+            Tg, alpha, v1, v2 = self.cia
+            c.cia_alpha, c.cia_T, c.cia_nT, c.cia_vmr1, c.cia_vmr2 = alpha.data_ptr(), Tg.data_ptr(), Tg.numel(), v1, v2
         return c
 
     def _struct_base(self, sp):
