@@ -176,6 +176,7 @@ def run_reference(args):
         vals.append(last["value"])
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
+    line_extra = oracle_other_configs()
     line = {"impl": "reference", "metric": "Voigt line x grid x layer evals/s", "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * wall / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
@@ -185,9 +186,41 @@ def run_reference(args):
                        "sample": "each step: oracle forward line sums at a random subset of (layer, point) pairs"},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "other_configs": line_extra}
     print(json.dumps(line))
     return 0
+
+
+def oracle_other_configs():
+    """The oracle on the single-layer case in full (2,000 lines, 4,096 points) and
+    on a few (layer, point) pairs of the 10,000,000 + 200,000-line case."""
+    import oracle
+    out = {}
+    lines, nu, T, P = W.single_layer_case()
+    t0 = time.perf_counter()
+    oracle.xs(lines, nu, T, P)
+    dt = time.perf_counter() - t0
+    ev = in_cut_triples(lines, nu, 25.0, 1)
+    out["single_layer_full"] = {"evals": ev, "seconds": dt, "evals_per_s": ev / dt}
+    cfg = W.WORKLOADS["scale"]
+    big = [W.water_like(cfg["n_water"]), W.co_like(cfg["n_co"])]
+    nu_s = W.grid_lognu(cfg["n_grid"])
+    p_s, _ = W.pressure_layers(cfg["n_layers"])
+    T_s = W.THETA_STAR[0] * p_s ** W.THETA_STAR[1]
+    li, gi = W.subset_pairs(cfg["n_layers"], cfg["n_grid"], 8 / (cfg["n_layers"] * cfg["n_grid"]))
+    ev, dt = 0, 0.0
+    lu, li_local = np.unique(li, return_inverse=True)  # pass only the sampled layers
+    for sp in big:
+        c = np.sort(sp.nu_hat)
+        per = (np.searchsorted(c, nu_s[gi] + 25.0, side="right") - np.searchsorted(c, nu_s[gi] - 25.0, side="left"))
+        t0 = time.perf_counter()
+        oracle.xs_points(sp, nu_s, T_s[lu], p_s[lu], li_local, gi)
+        dt += time.perf_counter() - t0
+        ev += int(per.sum())
+    out["scale_pairs"] = {"pairs": int(li.size), "evals": ev, "seconds": dt, "evals_per_s": ev / dt,
+                          "sample": "random (layer, point) pairs of the 10.2M-line case, both species"}
+    return out
 
 
 def serving(dev, closed_s, open_s):
