@@ -297,7 +297,8 @@ int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, 
  * No wing cut: each profile reaches half the period n_fft on either side.  n_fft
  * (a power of two, >= N + 2) is the padded period; for profiles that cover the
  * whole grid use n_fft >= 2 (N + m), m the farthest centre outside the grid in q
- * steps.  n_gamma 1..32.  Lines sorted by centre (as for xs_compute), device
+ * steps.  Lines whose centre lies more than (n_fft - N)/2 q steps outside the grid
+ * are left out.  n_gamma 1..32.  Lines sorted by centre (as for xs_compute), device
  * arrays; T, P_bar [L] device; sigma [L][N] device, double (XS_PREC_FP64:
  * FP64 distribution and FFT) or float (XS_PREC_MIXED: FP32 distribution and
  * FFT, strengths scaled by 2^80 inside).  The distribution is summed in a fixed
