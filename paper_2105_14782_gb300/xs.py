@@ -16,7 +16,7 @@ import torch
 
 from . import _build
 
-XS_OK, XS_EINVAL, XS_EUNSORTED, XS_ENOMEM, XS_ECUDA, XS_ETIMEOUT = 0, -1, -2, -3, -4, -5
+XS_OK, XS_EINVAL, XS_EUNSORTED, XS_ENOMEM, XS_ECUDA, XS_ETIMEOUT, XS_ETOOBIG = 0, -1, -2, -3, -4, -5, -6
 PREC_FP64, PREC_MIXED = 0, 1
 MAX_SPECIES = 8
 
