@@ -377,7 +377,8 @@ def ip_rv(F1, nu, nu_out, beta, rv):
 # ------------------------------------------------------------------ weak-line pre-filter (App. G)
 
 
-def contribution_filter(lines, p_bar, dp_bar, T_scan, vmr, g=1e5, mu=2.313, kappa_coef=1e-8, margin=2, sb=1.0):
+def contribution_filter(lines, p_bar, dp_bar, T_scan, vmr, g=1e5, mu=2.313, kappa_coef=1e-8, margin=2, sb=1.0,
+                        return_psi=False):
     """Lines that can contribute to the emission (App. G).  Per line: the isothermal
     temperature T* of the scan at which S(T) is largest (first on ties); at T*, the
     line-centre layer optical depths dtau_n = (dP_n/g)(vmr/(mu m_u)) S/(sqrt(2 pi) beta)
@@ -385,7 +386,8 @@ def contribution_filter(lines, p_bar, dp_bar, T_scan, vmr, g=1e5, mu=2.313, kapp
     line-centre cross-section); the contribution psi_n = exp(-tau_n) dtau_n P_n/dP_n with
     tau_n = sum_{k<=n} dtau_k; its argmax n_hat (first on ties).  The same for the grey
     continuum (kappa_coef P cm^2/g).  Returns (keep, n_hat per line, n_hat of the
-    continuum), keep = n_hat <= n_hat_cont + margin (layer index grows with pressure)."""
+    continuum), keep = n_hat <= n_hat_cont + margin (layer index grows with pressure);
+    with return_psi, also psi [L][n] of the lines, to tell which argmax are near-ties."""
     from scipy.special import erfcx
     p = np.asarray(p_bar, dtype=np.float64)
     dp = np.asarray(dp_bar, dtype=np.float64)
@@ -407,11 +409,36 @@ def contribution_filter(lines, p_bar, dp_bar, T_scan, vmr, g=1e5, mu=2.313, kapp
     dtau = tau([sig0], np.full((1, L), vmr), p, dp, g, mu, 0.0)
     dtc = tau([np.zeros((L, 1))], np.zeros((1, L)), p, dp, g, mu, kappa_coef)[:, 0]
 
-    def nhat(dt):
+    def contribution(dt):
         t = np.cumsum(dt, axis=0)
-        psi = np.exp(-t) * dt * (p / dp).reshape((L,) + (1,) * (dt.ndim - 1))
-        return np.argmax(psi, axis=0)
+        return np.exp(-t) * dt * (p / dp).reshape((L,) + (1,) * (dt.ndim - 1))
 
-    nh = nhat(dtau)
-    nc = int(nhat(dtc))
+    psi = contribution(dtau)
+    nh = np.argmax(psi, axis=0)
+    nc = int(np.argmax(contribution(dtc), axis=0))
+    if return_psi:
+        return nh <= nc + margin, nh, nc, psi
     return nh <= nc + margin, nh, nc
+
+
+# ------------------------------------------------------------------ layer temperature prior (Sec. 6.1)
+
+
+def gp_prior_layers(T, p_bar, T0, a_T=1e6, tau_P=10 ** 0.5, eps=1e-5):
+    """The Gaussian-process prior of the layer-by-layer retrieval (Sec. 6.1):
+    T ~ N(T0 u, K) with K_ij = a_T k_GP(log10 P_i - log10 P_j; tau_P) + eps a_T delta_ij
+    and the RBF kernel k_GP(x; tau) = exp(-x^2 / (2 tau^2)) of Sec. 5.2.3.
+    Returns (log p(T), d log p/dT [L], d log p/dT0) from the multivariate normal
+    density written out: log p = -r^T K^-1 r / 2 - log det K / 2 - (L/2) log 2 pi,
+    r = T - T0 u; d log p/dT = -K^-1 r; d log p/dT0 = u^T K^-1 r.  numpy's solve and
+    slogdet are the library steps."""
+    T = np.asarray(T, dtype=np.float64)
+    lp = np.log10(np.asarray(p_bar, dtype=np.float64))
+    L = T.size
+    K = a_T * np.exp(-(lp[:, None] - lp[None, :]) ** 2 / (2.0 * tau_P ** 2)) + eps * a_T * np.eye(L)
+    r = T - T0
+    x = np.linalg.solve(K, r)
+    sign, logdet = np.linalg.slogdet(K)
+    if sign <= 0:
+        return float("nan"), np.full(L, np.nan), float("nan")
+    return float(-0.5 * r @ x - 0.5 * logdet - 0.5 * L * np.log(2.0 * np.pi)), -x, float(np.sum(x))

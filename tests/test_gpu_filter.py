@@ -1,7 +1,10 @@
 """Weak-line pre-filter (App. G) on the GPU against the oracle: the layer of
-largest contribution for every line and the keep decision, identical except
-where the oracle's two largest contributions tie to 1e-12; the filtered list
-gives the same spectrum where the continuum hides the removed lines."""
+largest contribution for every line and the keep decision.  Where they differ,
+the GPU's layer must be a near-tie of the oracle's: its contribution psi within a
+relative 1e-9 of the oracle's largest (both sides compute psi in FP64, so only
+rounding separates them), and the keep decision may differ only on such lines.
+The filtered list gives the same spectrum where the continuum hides the removed
+lines."""
 import numpy as np
 import pytest
 
@@ -25,15 +28,25 @@ def test_filter_matches_oracle(xs):
     import oracle
     p, dp = W.pressure_layers(100)
     lines = W.water_like(20_000, seed=74)
-    keep_o, nh_o, nc = oracle.contribution_filter(lines, p, dp, T_SCAN, 1e-3, kappa_coef=0.1)
+    keep_o, nh_o, nc, psi_o = oracle.contribution_filter(lines, p, dp, T_SCAN, 1e-3, kappa_coef=0.1,
+                                                         return_psi=True)
     dl = xs.DeviceLines(lines)  # sorted by centre
     order = np.argsort(lines.nu_hat, kind="stable")
     P, DP = torch.as_tensor(p, device="cuda"), torch.as_tensor(dp, device="cuda")
     keep, nh = xs.contribution_filter(dl, P, DP, T_SCAN, 1e-3, kappa_coef=0.1)
     keep, nh = keep.cpu().numpy(), nh.cpu().numpy()
-    diff = np.nonzero(nh != nh_o[order])[0]
-    assert diff.size <= 2, diff.size  # only near-ties of the argmax may differ
-    assert np.array_equal(keep, keep_o[order]) or np.count_nonzero(keep != keep_o[order]) <= diff.size
+    nh_o, keep_o, psi_o = nh_o[order], keep_o[order], psi_o[:, order]
+    diff = np.nonzero(nh != nh_o)[0]
+    assert diff.size <= 20, diff.size
+    # every differing argmax is a valid one: a near-tie of the oracle's maximum
+    cols = np.arange(nh.size)
+    best = psi_o[nh_o, cols]
+    mine = psi_o[nh, cols]
+    assert np.all(mine[diff] >= (1.0 - 1e-9) * best[diff]), (diff, mine[diff] / best[diff])
+    # keep differs only where the argmax does, and then follows the GPU's own argmax
+    kdiff = np.nonzero(keep != keep_o)[0]
+    assert np.all(np.isin(kdiff, diff)), kdiff
+    assert np.array_equal(keep.astype(bool), nh <= nc + 2)
     assert 0 < keep.sum() < lines.nu_hat.size
 
 

@@ -124,7 +124,11 @@ def test_model_forward_and_gradient_match_oracle(xs, problem, theta):
         F = model.forward(theta).cpu().numpy()
         assert np.max(np.abs(F - F_o) / F_o) < tol_f, prec
         ll, g = model.logl_grad(theta)
-        assert ll == pytest.approx(ll_o, rel=tol_f * 1e3, abs=tol_f * 1e3)
+        # the likelihood of the GPU's own spectrum, and its distance from the oracle's
+        # bounded by the spectrum tolerance: |d logL| <= sum |r| |dF|/s + (1/2) sum (dF/s)^2
+        assert ll == pytest.approx(oracle.loglike(F, d, sig), rel=1e-12)
+        r, e = (d - F_o) / sig, tol_f * F_o / sig
+        assert abs(ll - ll_o) <= np.sum(np.abs(r) * e) + 0.5 * np.sum(e * e), (prec, ll, ll_o)
         scale = np.abs(g_o)
         assert np.all(np.abs(g - g_o) <= tol_g * scale + 1e-12 * scale.max()), (prec, g, g_o)
 
