@@ -38,7 +38,8 @@ typedef enum {
     XS_ENOMEM = -3,    /* reserved for host-side allocation failure */
     XS_ECUDA = -4,     /* a CUDA launch or runtime call failed */
     XS_ETIMEOUT = -5,  /* a bounded host-side wait ran out */
-    XS_ETOOBIG = -6    /* the problem needs more scratch than xs_compute_noalloc's fixed array */
+    XS_ETOOBIG = -6    /* the problem needs more scratch than a fixed or given area holds
+                          (xs_compute_noalloc's array; MODIT's reserve for cuFFT's work area) */
 } xs_status;
 
 typedef enum {
@@ -121,8 +122,10 @@ int xs_compute(const xs_lines* lines, const double* nu, int64_t N, const double*
  * device array inside libxs that every GPU loading the library holds until the
  * process exits.  Problems whose smallest plan (one layer at a time) needs more
  * than 64 MiB, i.e. xs_workspace_min_bytes(n, N, L, prec) > 64 MiB, are
- * rejected with XS_ETOOBIG before any launch (roughly n * 44 bytes plus split-K
- * partials of up to 64 * N * 8 bytes, at one layer per pass).
+ * rejected with XS_ETOOBIG before any launch.  That plan holds about n * 68
+ * bytes (XS_PREC_MIXED) or n * 96 bytes (XS_PREC_FP64) of per-line records, the
+ * near-pair sums (N * 8 bytes, mixed) and split-K partials (up to 64 * N * 8
+ * bytes); xs_workspace_min_bytes gives the exact figure.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current); make that first call
  * before any stream capture.  All calls on a device share the one array and

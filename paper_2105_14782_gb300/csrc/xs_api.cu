@@ -101,6 +101,12 @@ namespace {
 inline cudaStream_t S(xs_stream s) { return (cudaStream_t)s; }
 inline size_t al(size_t v) { return (v + 255) & ~(size_t)255; }
 inline bool prec_ok(int p) { return p == XS_PREC_FP64 || p == XS_PREC_MIXED; }
+using xsi::check_common;
+using xsi::check_lines;
+
+} // namespace
+
+namespace xsi {
 
 int check_lines(const xs_lines* ln)
 {
@@ -121,7 +127,7 @@ int check_common(const xs_lines* ln, const double* nu, int64_t N, const double* 
     return XS_OK;
 }
 
-} // namespace
+} // namespace xsi
 
 extern "C" {
 
@@ -134,7 +140,7 @@ const char* xs_strerror(int status)
     case XS_ENOMEM: return "out of host memory";
     case XS_ECUDA: return "CUDA error";
     case XS_ETIMEOUT: return "timed out";
-    case XS_ETOOBIG: return "problem exceeds the fixed scratch of xs_compute_noalloc";
+    case XS_ETOOBIG: return "problem needs more scratch memory than the fixed or given workspace holds";
     default: return "unknown status";
     }
 }

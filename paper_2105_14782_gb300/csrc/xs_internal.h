@@ -16,6 +16,11 @@ void prof_end(int kind, cudaStream_t st);
 
 enum { XS_RUN_KEEP_ADJ = 1, XS_RUN_REUSE = 2 };
 
+// argument checks shared by the entry points (XS_OK or XS_EINVAL, host side only)
+int check_lines(const xs_lines* ln);
+int check_common(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L,
+                 double sb, double W, int prec);
+
 // line-sum forward (adjoint == false: writes sigma) or adjoint (writes g_T, g_b);
 // flags as above (0 for a self-contained call)
 int xs_run(const xs_lines* ln, const double* nu, int64_t N, const double* T, const double* P, int32_t L, double sb,

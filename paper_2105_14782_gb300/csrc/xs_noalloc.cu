@@ -49,16 +49,14 @@ extern "C" int xs_compute_noalloc(const xs_lines* lines, const double* nu, int64
                                   const double* P_bar, int32_t L, double broad_scale, double wing_cut, int prec,
                                   void* sigma, xs_stream stream)
 {
-    if (!lines || lines->n < 0 || !nu || !T || !P_bar || !sigma || N <= 0 || L <= 0) return XS_EINVAL;
-    if (prec != XS_PREC_FP64 && prec != XS_PREC_MIXED) return XS_EINVAL;
-    if (lines->n > 0 && (!lines->nu_hat || !lines->ln_S0 || !lines->elower || !lines->gamma_ref || !lines->n_temp))
-        return XS_EINVAL;
-    if (!(wing_cut > 0.0) || !(broad_scale > 0.0) || !(lines->mass_amu > 0.0)) return XS_EINVAL;
-    if (lines->n >= ((int64_t)1 << 31) || N >= ((int64_t)1 << 31) - 2048) return XS_EINVAL;
+    // the same argument checks as xs_compute
+    int r = xsi::check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
+    if (r) return r;
+    if (!sigma) return XS_EINVAL;
     // the smallest plan (one layer at a time) must fit the fixed array
     if (xs_workspace_min_bytes(lines->n, N, L, prec) > XS_NOALLOC_SCRATCH_BYTES) return XS_ETOOBIG;
     void* scratch = nullptr;
-    int r = noalloc_scratch(&scratch);
+    r = noalloc_scratch(&scratch);
     if (r != XS_OK) return r;
     // Every scratch region the forward pass reads is written earlier in the same
     // call (cut ranges, per-layer minima, line records, split-K partials), so the

@@ -110,3 +110,4 @@ def test_new_entry_points_reject_bad_arguments_before_launch(lib):
     assert lib.xs_model_forward_keep(None, None, None, None, None, None) == -1
     lib.xs_model_logl_grad_layers.argtypes = [vp, vp, vp, C.c_double, vp, vp, vp, C.c_size_t, vp]
     assert lib.xs_model_logl_grad_layers(None, None, None, 1.0, None, None, None, 0, None) == -1
+
