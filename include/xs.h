@@ -366,10 +366,30 @@ int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu
  * layer): as xs_model_logl_grad with the power law replaced by T [L] (device,
  * Kelvin), log10_vmr [S] (host) and broad_scale; out [1 + L + S + 1] device:
  * logL, dlogL/dT_n for every layer, dlogL/dlog10 vmr_m, dlogL/d broad_scale.
- * A prior on the T_n (the paper's Gaussian process) is the caller's.
+ * The Gaussian-process prior on the T_n is the companion call gp_prior_layers.
  */
 int xs_model_logl_grad_layers(const xs_model* model, const double* T, const double* log10_vmr, double broad_scale,
                               double* out, double* F0, void* workspace, size_t workspace_bytes, xs_stream stream);
+
+/*
+ * Gaussian-process prior of the layer-by-layer temperatures (Sec. 6.1):
+ *   T ~ N(T0 u, K),  K_ij = a_T exp(-(log10 P_i - log10 P_j)^2 / (2 tau_P^2)) + eps a_T delta_ij
+ * (the RBF kernel of Sec. 5.2.3; the paper fixes a_T = 1e6, tau_P = 10^0.5, eps = 1e-5).
+ *   T, P_bar [L] device (Kelvin, bar), 1 <= L <= XS_GP_MAX_LAYERS
+ *   out [L + 2] device doubles: log p(T) (normalised density, with -(L/2) log 2 pi),
+ *       d log p / dT_n for every layer, d log p / dT0
+ * FP64 Cholesky factorisation of K in the workspace (gp_prior_workspace_bytes(L):
+ * L^2 + L doubles, caller-owned), one CTA, stream-ordered.  A K that is not
+ * positive definite in FP64 gives NaN in out[0] and out[L + 1].  XS_EINVAL for
+ * null pointers, L out of range, a_T <= 0, tau_P <= 0, eps < 0, a non-finite T0
+ * or a short workspace; XS_ECUDA on launch failure.  The posterior of the
+ * layer-by-layer retrieval is xs_model_logl_grad_layers' logL plus this log p,
+ * and its gradient in T_n the sum of the two.
+ */
+#define XS_GP_MAX_LAYERS 4096
+size_t gp_prior_workspace_bytes(int32_t L);
+int gp_prior_layers(const double* T, const double* P_bar, int32_t L, double T0, double a_T, double tau_P, double eps,
+                    double* out, void* workspace, size_t workspace_bytes, xs_stream stream);
 
 /*
  * The composite model as a vector-Jacobian product, for likelihoods that are not

@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libxs.so")
-SOURCES = ["xs_linesum.cu", "xs_rt.cu", "xs_api.cu", "xs_noalloc.cu", "xs_modit.cu", "xs_resp.cu", "xs_filter.cu"]
+SOURCES = ["xs_linesum.cu", "xs_rt.cu", "xs_api.cu", "xs_noalloc.cu", "xs_modit.cu", "xs_resp.cu", "xs_filter.cu",
+           "xs_prior.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

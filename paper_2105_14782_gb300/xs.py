@@ -104,6 +104,9 @@ def lib():
         L.modit_workspace_bytes.restype = sz
         L.modit_workspace_bytes.argtypes = [i64, i32, i32, i64, i]
         L.modit_compute.argtypes = [C.POINTER(XsLinesC), d, d, i64, vp, vp, i32, d, i32, i64, i, vp, vp, sz, vp]
+        L.gp_prior_workspace_bytes.restype = sz
+        L.gp_prior_workspace_bytes.argtypes = [i32]
+        L.gp_prior_layers.argtypes = [vp, vp, i32, d, d, d, d, vp, vp, sz, vp]
         _lib = L
     return _lib
 
@@ -365,6 +368,17 @@ def layer_temperatures(T0, alpha, P_bar, stream=None):
     _check("layer_temperatures", lib().layer_temperatures(float(T0), float(alpha), _dev(P_bar), P_bar.numel(),
                                                           _dev(T), _stream(stream)))
     return T
+
+
+def gp_prior_layers(T, P_bar, T0, a_T=1e6, tau_P=10 ** 0.5, eps=1e-5, stream=None):
+    """Gaussian-process prior of the layer temperatures (Sec. 6.1): device tensor
+    [log p(T), d log p/dT_0 .. d log p/dT_{L-1}, d log p/dT0]."""
+    L = T.numel()
+    out = torch.empty(L + 2, dtype=torch.float64, device=T.device)
+    ws = _ws(lib().gp_prior_workspace_bytes(L), T.device)
+    _check("gp_prior_layers", lib().gp_prior_layers(_dev(T), _dev(P_bar), L, float(T0), float(a_T), float(tau_P),
+                                                    float(eps), _dev(out), _dev(ws), ws.numel(), _stream(stream)))
+    return out
 
 
 def profile(enable: bool):
