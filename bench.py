@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the line-by-line emission model on GB300.
 
-One step = one HMC-style forward + gradient of the 100-layer emission workload
-(water-like 200,000 lines + CO-like 20,000 lines, 20,000-point log grid,
-W = 25 cm^-1): layer temperatures, both species' line-sum cross-sections,
-optical depth, emission solve, Gaussian log-likelihood, and the adjoints of all
-of them.  The metric counts Voigt evaluations: every in-cut (line, grid point,
-layer) triple is evaluated once in the forward line sum and once in its adjoint.
+One step = one HMC-style forward + gradient of the 100-layer emission model:
+layer temperatures, both species' line-sum cross-sections, optical depth,
+emission solve, Gaussian log-likelihood, and the adjoints of all of them, in the
+mixed precision form (FP32 Voigt and compensated sums, FP64 offsets and
+strengths, FP64 radiative transfer).  The metric counts Voigt evaluations: every
+in-cut (line, grid point, layer) triple is evaluated once in the forward line sum
+and once in its adjoint.
+
+The headline workload is the precision form at scale: 10,000,000 water-like +
+200,000 CO-like lines, a 100,000-point log grid over 4340-4390 cm^-1, 100 layers
+(1e-3 .. 1e2 bar), W = 25 cm^-1.  The emission workload (200,000 + 20,000 lines,
+20,000 points) is timed beside it under "extra".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -16,8 +22,8 @@ there is no data-path collective (weak scaling).
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -32,26 +38,43 @@ sys.path.insert(0, ROOT)
 
 import workloads as W  # noqa: E402
 
-FP32_LANES_PER_SM = 128
-N_SM = 152
-SM_MAX_MHZ = 2070.0
-FLOPS_PER_EVAL = {"fwd": 8, "adj": 12}  # cheapest packed wing forms (FFMA = 2, FADD = RCP = 1): a lower bound per evaluation
+T_START = time.perf_counter()
+# the whole command must end well inside the caller's limit (1,800 s): optional
+# legs are skipped, and say so, once the run gets near this budget
+WALL_BUDGET_S = 1500.0
 
+FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM on sm_103a (one FFMA = 2 flops)
 
-# DRAM bytes (read + write) per launch of linesum_adjoint_kernel<float>, averaged over
-# the two species, from one ncu capture of the 20-layer case scaled to 100 layers
-# (the traffic is per layer); valid only for the kernel sources it was taken on.
-TRAFFIC = {"kernel": "linesum_adjoint_kernel<float>", "bytes_per_launch_100_layers": 5.740e9,
-           "sources_sha256": "f5cdb344ad02c1e2914ba9f7025ba019a073d837c856a76c3a323d00356766ea"}
+# FP32 flops per in-cut triple of the two line-sum kernels, from the SASS
+# instruction counts of one ncu capture per workload (FFMA 2, FADD/FMUL 1, packed
+# FFMA2 4, FADD2/FMUL2 2 flops per thread instruction; MUFU reciprocals not
+# counted), divided by the launch's in-cut triples.  Valid only for the kernel
+# sources they were taken on (the hash); otherwise the bench falls back to the
+# cheapest-form lower bound and says so.
+FLOPS_PER_TRIPLE = {
+    "sources_sha256": "",
+    "emission": {"fwd": 9.17, "adj": 12.96,
+                 "capture": "water-like launch, 20-layer emission case (200,000 lines, 20,000 points)"},
+    "scale": None,
+}
+FLOPS_LOWER_BOUND = {"fwd": 8, "adj": 12}  # cheapest packed wing forms, RCP counted as 1 flop
+
+# DRAM bytes (read + write) per launch of the dominant kernel, from one ncu capture
+# of a reduced-layer case scaled by the layer count (traffic is per layer); null
+# unless the kernel sources still hash to the captured ones.
+TRAFFIC = {"sources_sha256": "", "kernel": "", "bytes_per_layer": None, "capture": ""}
 
 
 def kernel_sources_sha256():
-    import hashlib
     h = hashlib.sha256()
     for f in ("xs_linesum.cu", "xs_device.cuh"):
         with open(os.path.join(ROOT, "paper_2105_14782_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()
+
+
+def elapsed():
+    return time.perf_counter() - T_START
 
 
 def job_throughput(ms_local, evals_per_step, steps, world, dist=None, device="cpu"):
@@ -65,11 +88,14 @@ def job_throughput(ms_local, evals_per_step, steps, world, dist=None, device="cp
     return t_max, world * evals_per_step * steps / (t_max / 1000.0)
 
 
-def in_cut_triples(lines, nu, W_cut, L):
+def in_cut_counts(lines, nu, W_cut):
+    """In-cut lines per grid point (every layer has the same cut)."""
     c = np.sort(lines.nu_hat)
-    lo = np.searchsorted(nu, c - W_cut, side="left")
-    hi = np.searchsorted(nu, c + W_cut, side="right")
-    return int(np.sum(hi - lo)) * L
+    return np.searchsorted(c, nu + W_cut, side="right") - np.searchsorted(c, nu - W_cut, side="left")
+
+
+def in_cut_triples(lines, nu, W_cut, L):
+    return int(np.sum(in_cut_counts(lines, nu, W_cut))) * L
 
 
 def read_peaks():
@@ -78,6 +104,23 @@ def read_peaks():
             return json.load(f)
     except OSError:
         return {}
+
+
+WORKLOAD_TEXT = {
+    "scale": "precision form at scale: 100 layers 1e-3..1e2 bar, 10,000,000 water-like + 200,000 CO-like lines, "
+             "100,000-point log grid 4340-4390 cm^-1, W = 25 cm^-1",
+    "emission": "emission: 100 layers 1e-3..1e2 bar, 200,000 water-like + 20,000 CO-like lines, 20,000-point log "
+                "grid 4340-4390 cm^-1, W = 25 cm^-1",
+}
+
+
+def atmosphere(name, n_layers=100):
+    if name == "emission":
+        return W.emission_case(n_layers=n_layers)
+    cfg = W.WORKLOADS["scale"]
+    p, dp = W.pressure_layers(n_layers)
+    return W.Atmosphere(species=[W.water_like(cfg["n_water"]), W.co_like(cfg["n_co"])], vmr=[1e-3, 5e-4],
+                        nu=W.grid_lognu(cfg["n_grid"]), p_bar=p, dp_bar=dp)
 
 
 class ClockSampler:
@@ -114,7 +157,7 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], None, set()
+        sm, pw, mx, reasons = [], [], None, set()
         names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             p = [x.strip() for x in ln.split(",")]
@@ -123,110 +166,280 @@ class ClockSampler:
             try:
                 sm.append(float(p[1]))
                 mx = float(p[2])
+                pw.append(float(p[3]))
             except ValueError:
                 continue
             for nm, v in zip(names[1:], p[5:9]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "power_w_median": statistics.median(pw) if pw else None}
 
 
-def cpu_baseline(atm, budget_s=15.0):
-    """Oracle forward line sums at random (layer, grid point) pairs of the same
-    workload, on all host cores, sized to roughly budget_s seconds."""
+# ------------------------------------------------------------------ oracle legs (CPU)
+
+
+def oracle_pair_rate(species, nu, T, P, layer, gi, wing_cut=25.0):
+    """Oracle line sums at grid points gi of one layer, all species.  The oracle
+    first derives every line's parameters for the layer (one pass over the list);
+    that setup is timed on a call with no points and subtracted, so the rate is
+    that of the line sums themselves.  Returns (evaluations, seconds)."""
     import oracle
-    T = 1300.0 * atm.p_bar ** 0.1
-    L, N = len(atm.p_bar), len(atm.nu)
-    per_pair = sum(in_cut_triples(sp, atm.nu, atm.wing_cut, 1) for sp in atm.species) / N  # average triples per point
-    def timed(n):
-        li, gi = W.subset_pairs(L, N, n / (L * N))
+    ev, dt = 0, 0.0
+    li = np.zeros(gi.size, dtype=np.int32)
+    none_l, none_g = np.zeros(0, dtype=np.int32), np.zeros(0, dtype=np.int64)
+    for sp in species:
         t0 = time.perf_counter()
-        for sp in atm.species:
-            oracle.xs_points(sp, atm.nu, T, atm.p_bar, li, gi, wing_cut=atm.wing_cut)
-        return time.perf_counter() - t0
+        oracle.xs_points(sp, nu, T[layer:layer + 1], P[layer:layer + 1], none_l, none_g, wing_cut=wing_cut)
+        t1 = time.perf_counter()
+        oracle.xs_points(sp, nu, T[layer:layer + 1], P[layer:layer + 1], li, gi, wing_cut=wing_cut)
+        t2 = time.perf_counter()
+        ev += int(in_cut_counts(sp, nu[gi], wing_cut).sum())
+        dt += max((t2 - t1) - (t1 - t0), 1e-9)
+    return ev, dt
 
-    # t(n) = setup + n * per_pair: size the sample from two short probes
-    t_a, t_b = timed(32), timed(256)
-    per = max((t_b - t_a) / 224, t_b / 256 * 0.05, 1e-5)
-    n_pairs = int(min(20000, max(256, (budget_s - t_a) / per)))
-    li, gi = W.subset_pairs(L, N, n_pairs / (L * N))
-    t0 = time.perf_counter()
-    for sp in atm.species:
-        oracle.xs_points(sp, atm.nu, T, atm.p_bar, li, gi, wing_cut=atm.wing_cut)
-    dt = time.perf_counter() - t0
-    evals = per_pair * li.size
-    return {"value": evals / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"FP64 oracle forward line sums at {li.size} random (layer, grid point) pairs of the "
-                      f"emission workload, both species ({evals:.3g} Voigt evaluations, {dt:.1f} s)"}
+
+def cpu_baseline(atm, budget_s=15.0, seed=0):
+    """The FP64 oracle on a bounded sample of the same workload: random grid points
+    of one random layer, all species, on every host core; evaluations counted per
+    sampled point.  The sample holds at least 64 points so that the oracle's
+    parallel loop over points keeps every core busy."""
+    import oracle
+    rng = np.random.default_rng(W.SEED_SUBSET + 100 + seed)
+    T = W.THETA_STAR[0] * atm.p_bar ** W.THETA_STAR[1]
+    L, N = len(atm.p_bar), len(atm.nu)
+    per_point = sum(float(np.mean(in_cut_counts(sp, atm.nu, atm.wing_cut))) for sp in atm.species)
+    n_pts = int(max(64, min(20000, budget_s * 5e7 / per_point)))  # sized for ~5e7 evaluations/s
+    layer = int(rng.integers(L))
+    ev, dt = oracle_pair_rate(atm.species, atm.nu, T, atm.p_bar, layer, np.sort(rng.integers(0, N, n_pts)))
+    return {"value": ev / dt, "unit": "evals/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle forward line sums at {n_pts} random grid points of layer {layer}, all species "
+                      f"({ev:.3g} Voigt evaluations, {dt:.1f} s of line sums; the layer's one-pass line-parameter "
+                      "setup timed on a call with no points and excluded)"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    atm = W.emission_case()
-    for _ in range(args.warmup):
-        cpu_baseline(atm, budget_s=3.0)
+    atm = atmosphere(args.workload)
+    for i in range(args.warmup):
+        cpu_baseline(atm, budget_s=2.0, seed=1000 + i)
     vals = []
     t0 = time.perf_counter()
     last = None
-    for _ in range(args.steps):
-        last = cpu_baseline(atm, budget_s=10.0)
+    for i in range(args.steps):
+        last = cpu_baseline(atm, budget_s=8.0, seed=i)
         vals.append(last["value"])
     wall = time.perf_counter() - t0
     value = statistics.median(vals)
-    line_extra = oracle_other_configs()
     line = {"impl": "reference", "metric": "Voigt line x grid x layer evals/s", "value": value, "unit": "evals/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * wall / max(args.steps, 1), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "emission: 100 layers, 200,000 water-like + 20,000 CO-like lines, "
-                                   "20,000-point log grid, W = 25 cm^-1",
-                       "sample": "each step: oracle forward line sums at a random subset of (layer, point) pairs"},
+            "config": {"workload": WORKLOAD_TEXT[args.workload],
+                       "sample": "each step: oracle forward line sums at random grid points of one random layer"},
             "cpu_baseline": {"value": value, "unit": "evals/s", "cores": last["cores"], "kind": "oracle",
                              "sample": last["sample"]},
-            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "other_configs": line_extra}
+            "e2e": {"value": value, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def oracle_other_configs():
-    """The oracle on the single-layer case in full (2,000 lines, 4,096 points) and
-    on a few (layer, point) pairs of the 10,000,000 + 200,000-line case."""
-    import oracle
-    out = {}
-    lines, nu, T, P = W.single_layer_case()
-    t0 = time.perf_counter()
-    oracle.xs(lines, nu, T, P)
-    dt = time.perf_counter() - t0
-    ev = in_cut_triples(lines, nu, 25.0, 1)
-    out["single_layer_full"] = {"evals": ev, "seconds": dt, "evals_per_s": ev / dt}
-    cfg = W.WORKLOADS["scale"]
-    big = [W.water_like(cfg["n_water"]), W.co_like(cfg["n_co"])]
-    nu_s = W.grid_lognu(cfg["n_grid"])
-    p_s, _ = W.pressure_layers(cfg["n_layers"])
-    T_s = W.THETA_STAR[0] * p_s ** W.THETA_STAR[1]
-    li, gi = W.subset_pairs(cfg["n_layers"], cfg["n_grid"], 8 / (cfg["n_layers"] * cfg["n_grid"]))
-    ev, dt = 0, 0.0
-    lu, li_local = np.unique(li, return_inverse=True)  # pass only the sampled layers
-    for sp in big:
-        c = np.sort(sp.nu_hat)
-        per = (np.searchsorted(c, nu_s[gi] + 25.0, side="right") - np.searchsorted(c, nu_s[gi] - 25.0, side="left"))
-        t0 = time.perf_counter()
-        oracle.xs_points(sp, nu_s, T_s[lu], p_s[lu], li_local, gi)
-        dt += time.perf_counter() - t0
-        ev += int(per.sum())
-    out["scale_pairs"] = {"pairs": int(li.size), "evals": ev, "seconds": dt, "evals_per_s": ev / dt,
-                          "sample": "random (layer, point) pairs of the 10.2M-line case, both species"}
-    return out
+# ------------------------------------------------------------------ GPU legs
 
 
-def serving(dev, closed_s, open_s):
-    """Continuous-batching server under the HMC request mix: a saturated closed
-    loop (256 chains, 200 req/s offered), an open loop at 0.8x the capacity that
-    loop measured, and the FP64 path on a bounded sample of the same stream."""
+def timed_ms(fn, stream):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), r
+
+
+def error_block(dev, atm, model, theta, stream):
+    """Relative error of the mixed path against the FP64 GPU path on the same GPU,
+    per result, at theta:
+      sigma: every layer at a block of 256 consecutive grid points (seeded start),
+             both species, where sigma > 1e-6 of the layer maximum; the mixed values
+             come from the full-grid call in the step's launch configuration;
+      F0:    the model's spectrum at those points against the FP64 line sums
+             composed with the FP64 optical depth and emission solve;
+      gradient: logL over a 64-point window and its gradient, mixed vs FP64."""
+    import torch
+    from paper_2105_14782_gb300 import xs
+    f64 = dict(dtype=torch.float64, device=dev)
+    N, L = len(atm.nu), len(atm.p_bar)
+    rng = np.random.default_rng(W.SEED_SUBSET + 7)
+    j0 = int(rng.integers(0, N - 256))
+    blk = np.arange(j0, j0 + 256)
+    T = xs.layer_temperatures(theta[0], theta[1], model.P)
+    sb = float(theta[-1])
+    nu_b = torch.as_tensor(atm.nu[blk], **f64)
+    out, s64s = {}, []
+    worst, ms64, ev64 = 0.0, 0.0, 0
+    for k, dl in enumerate(model.species):
+        smx = xs.xs_compute(dl, model.nu, T, model.P, broad_scale=sb, wing_cut=atm.wing_cut, prec=xs.PREC_MIXED,
+                            workspace=model.ws)[:, blk].double()
+        ms, s64 = timed_ms(lambda: xs.xs_compute(dl, nu_b, T, model.P, broad_scale=sb, wing_cut=atm.wing_cut,
+                                                 prec=xs.PREC_FP64), stream)
+        ms64 += ms
+        ev64 += int(in_cut_counts(atm.species[k], atm.nu[blk], atm.wing_cut).sum()) * L
+        m = s64 > 1e-6 * s64.max(dim=1, keepdim=True).values
+        worst = max(worst, float(((smx - s64).abs() / s64)[m].max()))
+        s64s.append(s64)
+    out["sigma_max_rel"] = worst
+    S = len(model.species)
+    vmr = torch.as_tensor(np.array([[10.0 ** theta[2 + m]] * L for m in range(S)]), **f64)
+    dtau = xs.tau_layers(s64s, vmr, model.P, model.dP, atm.gravity, atm.mu, atm.kappa_coef, prec=xs.PREC_FP64)
+    F64 = xs.emission_spectrum(dtau, T, nu_b)
+    Fmx = model.F0[torch.as_tensor(blk, device=dev)]  # the spectrum of the last end-to-end step, at theta
+    out["F0_max_rel"] = float(((Fmx - F64).abs() / F64).max())
+    # gradient of logL over a 64-point window
+    w = blk[:64]
+    sub = W.Atmosphere(species=atm.species, vmr=atm.vmr, nu=atm.nu[w], p_bar=atm.p_bar, dp_bar=atm.dp_bar,
+                       wing_cut=atm.wing_cut, kappa_coef=atm.kappa_coef, gravity=atm.gravity, mu=atm.mu)
+    d_w, s_w = model.d_obs.cpu().numpy()[w], model.sig_obs.cpu().numpy()[w]
+    g = {}
+    for name, prec in (("mixed", xs.PREC_MIXED), ("fp64", xs.PREC_FP64)):
+        m = xs.EmissionModel(sub, prec=prec, device=dev, lines=model.species, d_obs=d_w, sig_obs=s_w)
+        g[name] = m.logl_grad_async(theta).cpu().numpy()
+        del m
+        torch.cuda.empty_cache()
+    rel = np.abs(g["mixed"] - g["fp64"]) / np.abs(g["fp64"])
+    out["logL_rel"] = float(rel[0])
+    out["grad_max_rel"] = float(rel[1:].max())
+    out["grad_rel"] = [float(v) for v in rel[1:]]
+    out["where"] = (f"sigma and F0: all {L} layers x grid points {j0}..{j0 + 255}; gradient: logL over grid "
+                    f"points {j0}..{j0 + 63}, theta = {[round(float(v), 4) for v in theta]}")
+    out["tolerance"] = {"sigma": 1e-5, "F0": 1e-6, "grad": 1e-4}
+    torch.cuda.empty_cache()
+    fp64 = {"forward_ms_256_points": ms64, "forward_evals_per_s": ev64 / (ms64 / 1000.0)}
+    return out, fp64
+
+
+def step_bench(dev, stream, atm, prec, steps, warmup, rank, world, dist, e2e_steps):
+    """Warm up, time `steps` forward + gradient steps (CUDA events on the launching
+    stream, barrier and synchronize on both sides), then the end-to-end steps."""
+    import torch
+    from paper_2105_14782_gb300 import xs
+    L, N = len(atm.p_bar), len(atm.nu)
+    triples = sum(in_cut_triples(sp, atm.nu, atm.wing_cut, L) for sp in atm.species)
+    model = xs.EmissionModel(atm, prec=prec, device=dev)
+    F_star = model.forward(W.THETA_STAR).clone()
+    sig = 0.01 * F_star
+    model.set_observation(F_star + sig * torch.as_tensor(W.std_normal(N), device=dev), sig)
+    theta = W.theta_points(64)[rank % 64]
+    for _ in range(warmup):
+        model.logl_grad_async(theta)
+    torch.cuda.synchronize(dev)
+
+    gpu_index = int(os.environ.get("LOCAL_RANK", "0"))
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        gpu_index = vis.split(",")[gpu_index]
+    clocks = ClockSampler(gpu_index)
+    clocks.start()
+    time.sleep(0.5)
+    xs.profile(True)
+    n0 = xs.launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        model.logl_grad_async(theta)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    launches = (xs.launch_count() - n0) / steps
+    prof = xs.profile_read()
+    xs.profile(False)
+    clk = clocks.stop()
+    assert np.all(np.isfinite(model.out.cpu().numpy())), "non-finite logL or gradient"
+    evals_per_step = 2 * triples
+    t_max, value = job_throughput(ms, evals_per_step, steps, world, dist, dev)
+
+    # end to end through the public API with host buffers: line lists, grid, layers
+    # and the observed spectrum go host -> device every step; logL, gradient and the
+    # spectrum come back
+    host = [[t.cpu().pin_memory() for t in sp.tensors] for sp in model.species]
+    host_misc = [x.cpu().pin_memory() for x in (model.nu, model.P, model.dP, model.d_obs, model.sig_obs)]
+    out_h = torch.empty(model.out.shape, dtype=torch.float64).pin_memory()
+    F_h = torch.empty(N, dtype=torch.float64).pin_memory()
+    h2d = sum(t.numel() * 8 for sp in host for t in sp) + sum(x.numel() * 8 for x in host_misc)
+    d2h = out_h.numel() * 8 + F_h.numel() * 8
+
+    def e2e_step():
+        for sp, hs in zip(model.species, host):
+            for dt_, ht in zip(sp.tensors, hs):
+                dt_.copy_(ht, non_blocking=True)
+        for dt_, ht in zip((model.nu, model.P, model.dP, model.d_obs, model.sig_obs), host_misc):
+            dt_.copy_(ht, non_blocking=True)
+        model.logl_grad_async(theta, F0=model.F0)
+        out_h.copy_(model.out, non_blocking=True)
+        F_h.copy_(model.F0, non_blocking=True)
+
+    torch.cuda.synchronize(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    e_ms = a.elapsed_time(b) / e2e_steps
+    assert np.all(np.isfinite(out_h.numpy())), "non-finite end-to-end result"
+    e2e = {"value": world * evals_per_step / (e_ms / 1000.0), "unit": "evals/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e_ms, "steps": e2e_steps}
+    return dict(model=model, theta=theta, triples=triples, evals_per_step=evals_per_step, ms=ms, t_max=t_max,
+                value=value, launches=launches, prof=prof, clocks=clk, e2e=e2e)
+
+
+def roofline(res, atm, workload, steps, n_sm, clk):
+    """The dominant line-sum kernel against the FP32 pipe: FP32 flops per launch
+    (flops per in-cut triple x the launch's triples) over its mean launch time."""
+    fwd_ms, fwd_n, adj_ms, adj_n = res["prof"]
+    kind = "adj" if adj_ms >= fwd_ms else "fwd"
+    k_ms = (adj_ms if kind == "adj" else fwd_ms) / max(adj_n if kind == "adj" else fwd_n, 1)
+    per_launch = res["triples"] / len(atm.species)  # one launch per species and step, averaged over species
+    fl = FLOPS_PER_TRIPLE.get(workload)
+    measured = bool(fl) and FLOPS_PER_TRIPLE["sources_sha256"] == kernel_sources_sha256()
+    fpt = fl[kind] if measured else FLOPS_LOWER_BOUND[kind]
+    achieved = per_launch * fpt / (k_ms / 1000.0) / 1e12
+    peaks = read_peaks()
+    sm_max = float(clk.get("sm_max_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    peak_max = n_sm * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sm_med = clk.get("sm_mhz") or sm_max
+    peak_med = n_sm * FP32_LANES_PER_SM * 2 * sm_med * 1e6 / 1e12
+    traffic = None
+    if TRAFFIC["bytes_per_layer"] and TRAFFIC["sources_sha256"] == kernel_sources_sha256() and \
+            TRAFFIC["kernel"] == kind:
+        traffic = TRAFFIC["bytes_per_layer"] * len(atm.p_bar)
+    name = "linesum_adjoint_kernel<float>" if kind == "adj" else "linesum_kernel<float>"
+    return {"bound": "alu", "achieved": achieved, "peak": peak_max, "unit": "TFLOP/s", "frac": achieved / peak_max,
+            "traffic": traffic, "kernel": name, "kernel_ms_per_launch": k_ms, "triples_per_launch": per_launch,
+            "flops_per_triple": fpt,
+            "flops_basis": (f"ncu SASS FP32 instruction counts ({fl['capture']})" if measured else
+                            "lower bound: cheapest packed wing form, ncu counts not taken on these sources"),
+            "peak_note": f"FP32 pipe: {n_sm} SMs (device) x {FP32_LANES_PER_SM} lanes x 2 flop x {sm_max:.0f} MHz "
+                         "(max SM clock); derived, not measured",
+            "frac_at_sampled_clock": achieved / peak_med, "sampled_sm_mhz": sm_med,
+            "traffic_note": TRAFFIC["capture"] or "no ncu DRAM capture on these sources"}
+
+
+def serving(dev, budget_s):
+    """Continuous-batching server under the HMC request mix (256 chains, 200 req/s
+    offered; line count log-uniform 1e3..1e6, grid 2,000..50,000, layers 20..200):
+    a saturated closed loop (the saturation point), then open-loop Poisson
+    arrivals at two fractions of the capacity it measured, each until at least
+    300 requests have completed, with latency binned by request size, and the
+    FP64 path on a bounded sample of the same stream."""
     import torch
     from paper_2105_14782_gb300 import serve, xs
 
@@ -242,18 +455,25 @@ def serving(dev, closed_s, open_s):
     sched.drain(timeout_s=120)
     setup_s = time.perf_counter() - t_setup
 
-    fin, wall = serve.closed_loop(sched, chains=256, offered_rate=200.0, duration_s=closed_s, cancel_at_end=True)
+    fin, wall = serve.closed_loop(sched, chains=256, offered_rate=200.0, duration_s=15.0, cancel_at_end=True)
     closed = serve.summarize(fin, wall)
-    closed.update(chains=256, offered_req_per_s=200.0, window_s=closed_s)
+    closed.update(chains=256, offered_req_per_s=200.0, window_s=15.0,
+                  note="saturated: 200 req/s offered against a capacity of a few req/s; its latencies are queueing "
+                       "under overload, not a sustained p99")
     cap = closed["evals_per_s"] / mean_ev
-
-    sched2 = serve.Scheduler(sched.ex, arena_bytes, slots)
-    sent, wall2 = serve.open_loop(sched2, rate=0.8 * cap, duration_s=open_s)
-    opened = serve.summarize(sent, wall2)
-    opened.update(offered_req_per_s=0.8 * cap, window_s=open_s)
-
-    # FP64 path vs the mixed path on the same requests, one at a time: the first
-    # requests of the stream whose work is at most 2e10 evaluations
+    slo = 4.0
+    points = []
+    for frac in (0.5, 0.8):
+        need_s = 330.0 / (frac * cap) + 5.0
+        if elapsed() + need_s > budget_s:
+            points.append({"load_fraction": frac, "skipped": f"time budget ({need_s:.0f} s needed)"})
+            continue
+        s2 = serve.Scheduler(sched.ex, arena_bytes, slots)
+        sent, wall2 = serve.open_loop(s2, rate=frac * cap, duration_s=need_s - 5.0, seed=W.SEED_SERVE + int(frac * 10))
+        st = serve.summarize(sent, wall2)
+        st.update(load_fraction=frac, offered_req_per_s=frac * cap, window_s=need_s - 5.0,
+                  by_size=serve.latency_by_size(sent), slo_met=st["p99_s"] <= slo)
+        points.append(st)
     sample = [r for r in serve.request_stream(400, seed=W.SEED_SERVE + 1)
               if 2 * r.n_layers * r.n_grid * r.n_lines * 0.75 <= 2e10][:6]
     res = {}
@@ -274,9 +494,9 @@ def serving(dev, closed_s, open_s):
     fp64 = {"evals_per_s": e64, "capacity_req_per_s": e64 / mean_ev, "latency_s": lat64,
             "mixed_evals_per_s_same_requests": emx, "mixed_latency_s": latmx,
             "sample": f"{len(sample)} requests of the stream with <= 2e10 evaluations each, run one at a time"}
-    del sched, sched2, pool
+    del sched, pool
     torch.cuda.empty_cache()
-    return {"closed_loop": closed, "open_loop_0p8_capacity": opened, "capacity_req_per_s": cap,
+    return {"slo_p99_s": slo, "open_loop": points, "closed_loop_saturation": closed, "capacity_req_per_s": cap,
             "mean_request_evals": mean_ev, "fp64_path": fp64, "slots": slots, "arena_bytes": arena_bytes,
             "setup_s": setup_s,
             "requests": "line count log-uniform 1e3..1e6 (served by the nearest of 7 resident water-like lists "
@@ -285,10 +505,10 @@ def serving(dev, closed_s, open_s):
             "latency": "submit to result on the host (pinned D2H of logL and gradient done)"}
 
 
-def modit_stats(dev, atm, scale_case=False):
+def modit_stats(dev, atm):
     """MODIT (Sec. 2.1.2) cross-sections of both species over all layers at theta*,
-    FP64 and FP32, timed with CUDA events, against the line-by-line sum (mixed,
-    W = 25 cm^-1) where that is above 1e-3 of its layer maximum."""
+    FP64 and FP32, against the line-by-line sum (mixed, W = 25 cm^-1) where that is
+    above 1e-3 of its layer maximum, and the forward + gradient step on MODIT."""
     import torch
     from paper_2105_14782_gb300 import xs
 
@@ -326,22 +546,20 @@ def modit_stats(dev, atm, scale_case=False):
             del ws
         out[name] = (ms, sig)
     res["fp64_ms"], res["fp32_ms"] = out["fp64"][0], out["fp32"][0]
-    if not scale_case:
-        ms = 0.0
-        lpf = []
-        for dl in lines:
-            t, r = timed(lambda: xs.xs_compute(dl, nu, T, P, prec=xs.PREC_MIXED))
-            ms += t
-            lpf.append(r.double())
-        res["lpf_mixed_ms"] = ms
-        d = []
-        for m, l in zip(out["fp64"][1], lpf):
-            mask = l > 1e-3 * l.max(dim=1, keepdim=True).values
-            d.append(((m - l).abs() / l)[mask])
-        d = torch.cat(d)
-        res["vs_lpf_rel_diff"] = {"median": float(d.median()), "p99": float(d.sort().values[int(0.99 * (d.numel() - 1))]),
-                                  "where": "sigma_LPF > 1e-3 of the layer maximum; LPF cut at 25 cm^-1, MODIT uncut"}
-    # the HMC step with MODIT cross-sections: forward + gradient of the emission model
+    ms = 0.0
+    lpf = []
+    for dl in lines:
+        t, r = timed(lambda: xs.xs_compute(dl, nu, T, P, prec=xs.PREC_MIXED))
+        ms += t
+        lpf.append(r.double())
+    res["lpf_mixed_ms"] = ms
+    d = []
+    for m, l in zip(out["fp64"][1], lpf):
+        mask = l > 1e-3 * l.max(dim=1, keepdim=True).values
+        d.append(((m - l).abs() / l)[mask])
+    d = torch.cat(d)
+    res["vs_lpf_rel_diff"] = {"median": float(d.median()), "p99": float(d.sort().values[int(0.99 * (d.numel() - 1))]),
+                              "where": "sigma_LPF > 1e-3 of the layer maximum; LPF cut at 25 cm^-1, MODIT uncut"}
     theta = W.theta_points(64)[0]
     for name, prec in (("fp64", xs.PREC_FP64), ("fp32", xs.PREC_MIXED)):
         mm = xs.EmissionModel(atm, prec=prec, device=dev, lines=lines, method="modit", n_gamma=16)
@@ -360,20 +578,19 @@ def modit_stats(dev, atm, scale_case=False):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=["scale", "emission"],
+                    help="headline workload: the 10.2M-line precision form at scale (default) or the emission case")
     ap.add_argument("--prec", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--layers", type=int, default=100,
+                    help="layer count of the headline workload (100; fewer only for small profiling cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison forward")
+    ap.add_argument("--no-errors", action="store_true", help="skip the mixed-vs-FP64 error block")
+    ap.add_argument("--no-extra", action="store_true", help="skip the emission-workload line")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-modit", action="store_true", help="skip the MODIT measurement")
-    ap.add_argument("--modit-scale", action="store_true",
-                    help="also time MODIT on 10,000,000 + 200,000 lines and a 100,000-point grid")
-    ap.add_argument("--layers", type=int, default=100,
-                    help="layer count of the emission workload (100; fewer only for small profiling cases)")
-    ap.add_argument("--serve-seconds", type=float, nargs=2, default=(15.0, 30.0),
-                    help="closed-loop and open-loop windows of the serving measurement")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -395,175 +612,82 @@ def main():
         dist.barrier()
     from paper_2105_14782_gb300 import xs
 
-    prec = xs.PREC_MIXED if args.prec == "mixed" else xs.PREC_FP64
-    atm = W.emission_case(n_layers=args.layers)
-    L, N = len(atm.p_bar), len(atm.nu)
-    triples = sum(in_cut_triples(sp, atm.nu, atm.wing_cut, L) for sp in atm.species)
-    evals_per_step = 2 * triples  # forward + adjoint evaluation of every in-cut triple
-
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    model = xs.EmissionModel(atm, prec=prec, device=dev)
-    theta_star = W.THETA_STAR
-    F_star = model.forward(theta_star).clone()
-    sig = 0.01 * F_star
-    d = F_star + sig * torch.as_tensor(W.std_normal(N), device=dev)
-    model.set_observation(d, sig)
-    theta = W.theta_points(64)[rank % 64]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    prec = xs.PREC_MIXED if args.prec == "mixed" else xs.PREC_FP64
+    atm = atmosphere(args.workload, args.layers)
+    e2e_steps = max(1, min(2, args.steps))
+    res = step_bench(dev, stream, atm, prec, args.steps, args.warmup, rank, world, dist, e2e_steps)
+    t_max = res["t_max"]
+    roof = roofline(res, atm, args.workload, args.steps, n_sm, res["clocks"])
+    fwd_ms, fwd_n, adj_ms, adj_n = res["prof"]
+    skipped = []
 
-    for _ in range(args.warmup):
-        model.logl_grad_async(theta)
-    torch.cuda.synchronize(dev)
-
-    gpu_index = local
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
-    if vis:
-        gpu_index = vis.split(",")[local]
-    clocks = ClockSampler(gpu_index)
-    clocks.start()
-    time.sleep(0.5)
-    xs.profile(True)
-    n0 = xs.launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize(dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        model.logl_grad_async(theta)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    if world > 1:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
-    launches = (xs.launch_count() - n0) / args.steps
-    fwd_ms, fwd_n, adj_ms, adj_n = xs.profile_read()
-    xs.profile(False)
-    clk = clocks.stop()
-    out = model.out.cpu().numpy()
-    assert np.all(np.isfinite(out)), "non-finite logL or gradient"
-
-    t_max, value = job_throughput(ms, evals_per_step, args.steps, world, dist, dev)
-    ms_per_step = t_max / args.steps
-
-    # end to end through the public API with host buffers: line lists, grid, layers
-    # and the observed spectrum go host -> device every step; logL, gradient and the
-    # spectrum come back.
-    e2e = None
-    if rank == 0 or world > 1:
-        host = [[t.cpu().pin_memory() for t in sp.tensors] for sp in model.species]
-        host_misc = [x.cpu().pin_memory() for x in (model.nu, model.P, model.dP, model.d_obs, model.sig_obs)]
-        out_h = torch.empty(model.out.shape, dtype=torch.float64).pin_memory()
-        F_h = torch.empty(N, dtype=torch.float64).pin_memory()
-        h2d = sum(t.numel() * 8 for sp in host for t in sp) + sum(x.numel() * 8 for x in host_misc)
-        d2h = out_h.numel() * 8 + F_h.numel() * 8
-
-        def e2e_step():
-            for sp, hs in zip(model.species, host):
-                for dt_, ht in zip(sp.tensors, hs):
-                    dt_.copy_(ht, non_blocking=True)
-            for dt_, ht in zip((model.nu, model.P, model.dP, model.d_obs, model.sig_obs), host_misc):
-                dt_.copy_(ht, non_blocking=True)
-            model.logl_grad_async(theta, F0=model.F0)
-            out_h.copy_(model.out, non_blocking=True)
-            F_h.copy_(model.F0, non_blocking=True)
-
-        for _ in range(2):
-            e2e_step()
-        torch.cuda.synchronize(dev)
-        k = max(2, args.steps // 2)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(k):
-            e2e_step()
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        e_ms = a.elapsed_time(b) / k
-        e2e = {"value": world * evals_per_step / (e_ms / 1000.0), "unit": "evals/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
-
-    # dominant kernel roofline (ALU bound, FP32 pipe)
-    peaks = read_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", SM_MAX_MHZ))
-    fp32_peak = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    per_step_fwd = fwd_ms / args.steps
-    per_step_adj = adj_ms / args.steps
-    kind = "adj" if per_step_adj >= per_step_fwd else "fwd"
-    k_ms = adj_ms if kind == "adj" else fwd_ms
-    k_n = adj_n if kind == "adj" else fwd_n
-    # launches per step = one per species; triples per launch averaged over species
-    avg_triples = triples / len(atm.species)
-    achieved = avg_triples * FLOPS_PER_EVAL[kind] / ((k_ms / max(k_n, 1)) / 1000.0) / 1e12
-    traffic = None
-    if (kind == "adj" and len(atm.p_bar) == 100 and kernel_sources_sha256() == TRAFFIC["sources_sha256"]):
-        traffic = TRAFFIC["bytes_per_launch_100_layers"]
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak, "traffic": traffic,
-                "traffic_note": "ncu dram bytes per launch (20-layer capture x 5); null once the kernel changed",
-                "kernel": "linesum_adjoint_kernel<float>" if kind == "adj" else "linesum_kernel<float>",
-                "peak_note": "FP32 pipe: 152 SMs x 128 lanes x 2 flop x max SM clock (derived, not measured)",
-                "flops_per_eval": FLOPS_PER_EVAL[kind]}
-
-    fp64 = None
-    if not args.no_fp64 and rank == 0:
-        # one timed call: it lasts tens of seconds, so loading the FP64 kernels on
-        # their first launch (milliseconds) does not show in it
-        m64 = xs.EmissionModel(atm, prec=xs.PREC_FP64, device=dev, lines=model.species)
-        torch.cuda.synchronize(dev)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        m64.forward(theta)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        f64_ms = a.elapsed_time(b)
-        a.record(stream)
-        model.forward(theta)
-        b.record(stream)
-        torch.cuda.synchronize(dev)
-        mix_ms = a.elapsed_time(b)
-        fp64 = {"forward_ms": f64_ms, "forward_evals_per_s": triples / (f64_ms / 1000.0),
-                "mixed_forward_ms": mix_ms, "speedup_mixed_vs_fp64": f64_ms / mix_ms}
-        del m64
+    errors, fp64 = None, None
+    if rank == 0 and not args.no_errors and prec == xs.PREC_MIXED:
+        if elapsed() < WALL_BUDGET_S - 300:
+            errors, fp64 = error_block(dev, atm, res["model"], res["theta"], stream)
+        else:
+            skipped.append("errors")
+    del res["model"]
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(atm)
 
+    extra = None
+    if rank == 0 and world == 1 and not args.no_extra and args.workload == "scale":
+        if elapsed() < WALL_BUDGET_S - 200:
+            em = atmosphere("emission")
+            r2 = step_bench(dev, stream, em, prec, 20, 3, rank, 1, None, 4)
+            rf2 = roofline(r2, em, "emission", 20, n_sm, r2["clocks"])
+            extra = {"emission": {"workload": WORKLOAD_TEXT["emission"], "value": r2["value"], "unit": "evals/s",
+                                  "ms_per_step": r2["t_max"] / 20, "steps": 20, "warmup": 3,
+                                  "evals_per_step": r2["evals_per_step"], "e2e": r2["e2e"], "roofline": rf2,
+                                  "clocks": r2["clocks"], "gpu_launches": r2["launches"]}}
+            del r2
+            torch.cuda.empty_cache()
+        else:
+            skipped.append("extra")
+
     modit = None
     if rank == 0 and world == 1 and not args.no_modit:
-        modit = {"emission": modit_stats(dev, atm)}
-        if args.modit_scale:
-            cfg = W.WORKLOADS["scale"]
-            p_, dp_ = W.pressure_layers(cfg["n_layers"])
-            big = W.Atmosphere(species=[W.water_like(cfg["n_water"]), W.co_like(cfg["n_co"])], vmr=[1e-3, 5e-4],
-                               nu=W.grid_lognu(cfg["n_grid"]), p_bar=p_, dp_bar=dp_)
-            modit["scale"] = modit_stats(dev, big, scale_case=True)
-        torch.cuda.empty_cache()
+        if elapsed() < WALL_BUDGET_S - 200:
+            modit = {"emission": modit_stats(dev, atmosphere("emission"))}
+            torch.cuda.empty_cache()
+        else:
+            skipped.append("modit")
 
     serve_stats = None
     if rank == 0 and world == 1 and not args.no_serve:
-        del model
-        torch.cuda.empty_cache()
-        serve_stats = serving(dev, *args.serve_seconds)
+        if elapsed() < WALL_BUDGET_S - 120:
+            serve_stats = serving(dev, WALL_BUDGET_S)
+        else:
+            skipped.append("serving")
 
     if rank == 0:
-        line = {"metric": "Voigt line x grid x layer evals/s", "value": value, "unit": "evals/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == xs.PREC_MIXED else "f64",
-                "data": "synthetic",
-                "config": {"workload": f"emission: {L} layers 1e-3..1e2 bar, 200,000 water-like + 20,000 CO-like "
-                                       "lines, 20,000-point log grid 4340-4390 cm^-1, W = 25 cm^-1",
+        L, N = len(atm.p_bar), len(atm.nu)
+        line = {"metric": "Voigt line x grid x layer evals/s", "value": res["value"], "unit": "evals/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if prec == xs.PREC_MIXED else "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD_TEXT[args.workload] if L == 100 else
+                           WORKLOAD_TEXT[args.workload].replace("100 layers", f"{L} layers"),
                            "step": "forward + gradient (logL and dlogL/dtheta, theta = T0, alpha, 2 log10 VMR, "
                                    "broadening scale)",
                            "precision": "FP32 Voigt + compensated FP32 sums, FP64 offsets/strengths, FP64 RT"
                            if prec == xs.PREC_MIXED else "FP64 throughout",
-                           "evals_per_step": evals_per_step, "in_cut_triples": triples,
-                           "l2": "per-step working set (line records rewritten every step, 0.95 GB) exceeds L2",
+                           "evals_per_step": res["evals_per_step"], "in_cut_triples": res["triples"],
+                           "l2": "inputs larger than L2: the per-step line records (tens of GB) are rewritten "
+                                 "every step",
                            "parallelism": f"replicas x{world}"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": launches,
-                "kernel_ms_per_step": {"linesum_fwd": per_step_fwd, "linesum_adj": per_step_adj},
-                "fp64_path": fp64, "serving": serve_stats, "modit": modit}
+                "roofline": roof, "cpu_baseline": cpu, "e2e": res["e2e"], "clocks": res["clocks"],
+                "gpu_launches": res["launches"],
+                "kernel_ms_per_step": {"linesum_fwd": fwd_ms / args.steps, "linesum_adj": adj_ms / args.steps},
+                "errors": errors, "fp64_path": fp64, "extra": extra, "serving": serve_stats, "modit": modit,
+                "skipped": skipped, "wall_s": elapsed()}
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
