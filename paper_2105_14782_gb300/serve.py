@@ -247,6 +247,19 @@ class LibxsExecutor:
         self.prec = prec
         self.fail_hook = fail_hook
         self.lib = xs.lib()
+        # per-slot pinned host staging, allocated once (grown only for a larger
+        # request): a slot's next request starts after its previous one completed,
+        # so its copies have drained
+        self.stage = [None] * len(streams)
+        self.outs = [torch.empty(8, dtype=torch.float64).pin_memory() for _ in streams]
+
+    def _staging(self, slot, n):
+        buf = self.stage[slot]
+        if buf is None or buf.numel() < n:
+            cap = max(n, 4 * 50_000 + 2 * 1000, 0 if buf is None else 2 * buf.numel())
+            buf = self.torch.empty(cap, dtype=self.torch.float64).pin_memory()
+            self.stage[slot] = buf
+        return buf
 
     def valid(self, r):
         return r.n_lines >= 1 and 2 <= r.n_grid <= 2_000_000 and 1 <= r.n_layers <= 1000 and np.all(np.isfinite(r.theta))
@@ -288,8 +301,13 @@ class LibxsExecutor:
         N, L = r.n_grid, r.n_layers
         nu = W.grid_lognu(N)
         P, dP = W.pressure_layers(L)
-        host = torch.from_numpy(np.concatenate([nu, P, dP, np.ones(N), np.full(N, 0.01)])).pin_memory()
         sizes = [N, L, L, N, N]
+        host = self._staging(slot, sum(sizes))
+        hn = host.numpy()
+        o = 0
+        for v in (nu, P, dP, np.ones(N), np.full(N, 0.01)):
+            hn[o:o + v.size] = v
+            o += v.size
         with torch.cuda.stream(st):
             o = 0
             for key, n in zip(("nu", "P", "dP", "d", "s"), sizes):
@@ -302,7 +320,7 @@ class LibxsExecutor:
                                            lay["ws"][1], C.c_void_p(st.cuda_stream))
         if code != 0:
             raise RuntimeError(f"xs_model_logl_grad: {code}")
-        out_h = torch.empty(6, dtype=torch.float64).pin_memory()
+        out_h = self.outs[slot][:6]
         with torch.cuda.stream(st):
             out_h.copy_(self.arena_t.narrow(0, off0 + lay["out"][0], 48).view(torch.float64), non_blocking=True)
             ev = torch.cuda.Event()
@@ -404,6 +422,21 @@ def mean_request_evals(pool: LinePool, n=100_000, seed=W.SEED_SERVE):
     nl, ng, nlay = W.serving_requests(n, seed)
     fr = np.array([pool.cut_fraction(pool.nearest(int(v))) for v in nl]) + pool.co_fraction
     return float(np.mean(2.0 * nlay * ng * fr))
+
+
+SIZE_BINS = (0.0, 1e10, 1e11, 1e12, 1e13, float("inf"))
+
+
+def latency_by_size(finished, bins=SIZE_BINS):
+    """p50/p99 latency of completed requests binned by their work (Voigt evaluations)."""
+    ok = [r for r in finished if r.status == DONE]
+    out = []
+    for lo, hi in zip(bins[:-1], bins[1:]):
+        lat = np.array([r.latency for r in ok if lo <= r.evals < hi])
+        if lat.size:
+            out.append({"evals_from": lo, "evals_to": hi, "count": int(lat.size),
+                        "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99))})
+    return out
 
 
 def summarize(finished, wall_s):
