@@ -85,6 +85,22 @@ int xs_sort_lines_host(int64_t n, double* nu_hat, double* ln_S0, double* elower,
  */
 int xs_check_sorted(const double* v, int64_t n, int strict, int* flag_dev, xs_stream stream);
 
+/*
+ * Bounds-checked build.  Compiled with -DXS_CHECKED (the library file
+ * libxs_checked.so), the kernels test the indices they derive from data (line
+ * windows, near ranges, cut ranges, grid indices, series table offsets) before
+ * each access; a failed test skips the access and records the source line in a
+ * device status word of its source file -- no trap, no fault.
+ * xs_checked_build: 1 in that build, 0 in the normal one (where the tests are
+ * compiled out).
+ * xs_check_status: synchronises the device, then returns 0 if no check failed
+ * since the last clear, else file * 100000 + line of a failed check (file 1 line
+ * sums, 2 radiative transfer, 3 MODIT, 4 responses, 5 pre-filter, 6 prior), or
+ * XS_ECUDA; with clear != 0 the words are reset.  Always 0 in the normal build.
+ */
+int xs_checked_build(void);
+int xs_check_status(int clear);
+
 /* Workspace bytes xs_compute / xs_compute_adjoint need for these sizes.  A
  * workspace down to xs_workspace_min_bytes still works (layers are then done in
  * chunks); sizes in between pick the largest chunk that fits. */

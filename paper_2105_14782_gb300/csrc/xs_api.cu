@@ -131,6 +131,30 @@ int check_common(const xs_lines* ln, const double* nu, int64_t N, const double* 
 
 extern "C" {
 
+int xs_checked_build(void)
+{
+#ifdef XS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int xs_check_status(int clear)
+{
+    XS_NVTX("xs_check_status");
+    if (cudaDeviceSynchronize() != cudaSuccess) return XS_ECUDA;
+    int (*const f[])(int) = {xsi::check_status_linesum, xsi::check_status_rt, xsi::check_status_modit,
+                             xsi::check_status_resp, xsi::check_status_filter, xsi::check_status_prior};
+    int worst = 0;
+    for (int i = 0; i < 6; ++i) {
+        const int v = f[i](clear);
+        if (v < 0) return XS_ECUDA;
+        if (v > 0 && worst == 0) worst = (i + 1) * 100000 + v;
+    }
+    return worst;
+}
+
 const char* xs_strerror(int status)
 {
     switch (status) {
@@ -164,6 +188,7 @@ int xs_sort_lines_host(int64_t n, double* nu_hat, double* ln_S0, double* elower,
 
 int xs_check_sorted(const double* v, int64_t n, int strict, int* flag_dev, xs_stream stream)
 {
+    XS_NVTX("xs_check_sorted");
     if (n < 0 || (n > 0 && !v) || !flag_dev) return XS_EINVAL;
     return xsi::check_sorted(v, n, S(stream), flag_dev, strict != 0);
 }
@@ -172,6 +197,7 @@ int xs_compute(const xs_lines* lines, const double* nu, int64_t N, const double*
                double broad_scale, double wing_cut, int prec, void* sigma, void* workspace, size_t workspace_bytes,
                xs_stream stream)
 {
+    XS_NVTX("xs_compute");
     int r = check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
     if (r) return r;
     if (!sigma || !workspace) return XS_EINVAL;
@@ -184,6 +210,7 @@ int xs_compute_adjoint(const xs_lines* lines, const double* nu, int64_t N, const
                        int32_t L, double broad_scale, double wing_cut, int prec, const double* g_sigma, double* g_T,
                        double* g_broad, void* workspace, size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("xs_compute_adjoint");
     int r = check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
     if (r) return r;
     if (!g_sigma || !g_T || !g_broad || !workspace) return XS_EINVAL;
@@ -196,6 +223,7 @@ int tau_layers(const void* const* sigma, int32_t nsp, const double* vmr, const d
                int32_t L, int64_t N, double gravity, double mu, double kappa_coef, int prec, double* dtau,
                xs_stream stream)
 {
+    XS_NVTX("tau_layers");
     if (!sigma || nsp < 1 || nsp > XS_MAX_SPECIES || !vmr || !P_bar || !dP_bar || L <= 0 || N <= 0 || !dtau)
         return XS_EINVAL;
     for (int m = 0; m < nsp; ++m)
@@ -208,6 +236,7 @@ int tau_layers_adjoint(const void* const* sigma, int32_t nsp, const double* vmr,
                        const double* dP_bar, int32_t L, int64_t N, double gravity, double mu, int prec,
                        const double* g_dtau, double* const* g_sigma, double* g_vmr, xs_stream stream)
 {
+    XS_NVTX("tau_layers_adjoint");
     if (!sigma || nsp < 1 || nsp > XS_MAX_SPECIES || !vmr || !P_bar || !dP_bar || L <= 0 || N <= 0 || !g_dtau ||
         !g_vmr)
         return XS_EINVAL;
@@ -221,6 +250,7 @@ int tau_layers_adjoint(const void* const* sigma, int32_t nsp, const double* vmr,
 int emission_spectrum(const double* dtau, const double* T, const double* nu, int32_t L, int64_t N, double* F0,
                       xs_stream stream)
 {
+    XS_NVTX("emission_spectrum");
     if (!dtau || !T || !nu || L <= 0 || N <= 0 || !F0) return XS_EINVAL;
     return xsi::rt_emission(dtau, T, nu, L, N, F0, S(stream));
 }
@@ -229,6 +259,7 @@ int tau_cia(const double* alpha, const double* T_grid, int32_t nT, const double*
             const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2, double gravity, double mu,
             int accumulate, double* dtau, xs_stream stream)
 {
+    XS_NVTX("tau_cia");
     if (!alpha || !T_grid || nT < 1 || !T || !P_bar || !dP_bar || L <= 0 || N <= 0 || !dtau) return XS_EINVAL;
     if (!(gravity > 0.0) || !(mu > 0.0) || !(vmr1 >= 0.0) || !(vmr2 >= 0.0)) return XS_EINVAL;
     return xsi::rt_tau_cia(alpha, T_grid, nT, T, P_bar, dP_bar, L, N, vmr1, vmr2, gravity, mu, accumulate != 0, dtau,
@@ -239,6 +270,7 @@ int tau_cia_adjoint(const double* g_dtau, const double* alpha, const double* T_g
                     const double* P_bar, const double* dP_bar, int32_t L, int64_t N, double vmr1, double vmr2,
                     double gravity, double mu, double* g_T, xs_stream stream)
 {
+    XS_NVTX("tau_cia_adjoint");
     if (!g_dtau || !alpha || !T_grid || nT < 1 || !T || !P_bar || !dP_bar || L <= 0 || N <= 0 || !g_T)
         return XS_EINVAL;
     if (!(gravity > 0.0) || !(mu > 0.0)) return XS_EINVAL;
@@ -256,6 +288,7 @@ int emission_spectrum_adjoint(const double* g_F0, const double* dtau, const doub
                               int64_t N, double* g_dtau, double* g_T, void* workspace, size_t workspace_bytes,
                               xs_stream stream)
 {
+    XS_NVTX("emission_spectrum_adjoint");
     if (!g_F0 || !dtau || !T || !nu || L <= 0 || N <= 0 || !g_dtau || !g_T || !workspace) return XS_EINVAL;
     if (workspace_bytes < emission_workspace_bytes(L, N)) return XS_EINVAL;
     return xsi::rt_emission_adjoint(g_F0, dtau, T, nu, L, N, g_dtau, g_T, workspace, S(stream));
@@ -264,12 +297,14 @@ int emission_spectrum_adjoint(const double* g_F0, const double* dtau, const doub
 int loglike_gauss(const double* F, const double* d, const double* s, int64_t N, double* logL, double* g_F,
                   xs_stream stream)
 {
+    XS_NVTX("loglike_gauss");
     if (!F || !d || !s || N <= 0 || !logL) return XS_EINVAL;
     return xsi::rt_loglike(F, d, s, N, logL, g_F, S(stream));
 }
 
 int layer_temperatures(double T0, double alpha, const double* P_bar, int32_t L, double* T, xs_stream stream)
 {
+    XS_NVTX("layer_temperatures");
     if (!P_bar || !T || L <= 0 || !(T0 > 0.0) || !std::isfinite(alpha)) return XS_EINVAL;
     return xsi::rt_temperatures(T0, alpha, P_bar, L, T, S(stream));
 }
@@ -410,6 +445,7 @@ size_t xs_model_workspace_bytes(const xs_model* model)
 int xs_model_forward(const xs_model* model, const double* theta, double* F0, void* workspace, size_t workspace_bytes,
                      xs_stream stream)
 {
+    XS_NVTX("xs_model_forward");
     int r = check_model(model);
     if (r) return r;
     if (!theta || !F0 || !workspace) return XS_EINVAL;
@@ -491,6 +527,7 @@ extern "C" {
 int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, double* F0, void* workspace,
                        size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("xs_model_logl_grad");
     ModelPlan p;
     int r = model_args(m, theta, workspace, workspace_bytes, &p);
     if (r) return r;
@@ -508,6 +545,7 @@ int xs_model_logl_grad(const xs_model* m, const double* theta, double* out, doub
 int xs_model_logl_grad_layers(const xs_model* m, const double* T, const double* log10_vmr, double broad_scale,
                               double* out, double* F0, void* workspace, size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("xs_model_logl_grad_layers");
     if (!m || !T || !log10_vmr || m->n_species < 1 || m->n_species > XS_MAX_SPECIES) return XS_EINVAL;
     // theta in the composite layout with placeholder T0 = 1, alpha = 0 (unused)
     double theta[3 + XS_MAX_SPECIES];
@@ -532,6 +570,7 @@ int xs_model_logl_grad_layers(const xs_model* m, const double* T, const double* 
 int xs_model_forward_keep(const xs_model* m, const double* theta, double* F0, void* workspace,
                           size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("xs_model_forward_keep");
     ModelPlan p;
     int r = model_args(m, theta, workspace, workspace_bytes, &p);
     if (r) return r;
@@ -542,6 +581,7 @@ int xs_model_forward_keep(const xs_model* m, const double* theta, double* F0, vo
 int xs_model_vjp(const xs_model* m, const double* theta, const double* g_F0, double* out, void* workspace,
                  size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("xs_model_vjp");
     ModelPlan p;
     int r = model_args(m, theta, workspace, workspace_bytes, &p);
     if (r) return r;

@@ -71,6 +71,41 @@ template <> struct Tier<double> {
     static constexpr double tcut = 6.5;
 };
 
+// Bounds-checked build (nvcc -DXS_CHECKED): index checks guard the kernels'
+// global and shared accesses.  A failed check records its source line in this
+// translation unit's device status word (the largest line wins) and the access is
+// skipped, so a bad index never faults or traps; xs_check_status reads the words.
+// In the normal build XS_CHECK(c) is the constant true and costs nothing.
+#ifdef XS_CHECKED
+static __device__ int g_xs_check_line = 0;
+__device__ __forceinline__ bool xs_check(bool ok, int line)
+{
+    if (!ok) atomicMax(&g_xs_check_line, line);
+    return ok;
+}
+#define XS_CHECK(c) ::xsd::xs_check((c), __LINE__)
+// host accessor of this translation unit's word (read, then cleared if asked)
+#define XS_CHECK_ACCESSOR(name)                                                                      \
+    namespace xsi {                                                                                  \
+    int check_status_##name(int clear)                                                               \
+    {                                                                                                \
+        int v = 0;                                                                                   \
+        if (cudaMemcpyFromSymbol(&v, ::xsd::g_xs_check_line, sizeof(int)) != cudaSuccess) return -1; \
+        if (clear) {                                                                                 \
+            const int z = 0;                                                                         \
+            if (cudaMemcpyToSymbol(::xsd::g_xs_check_line, &z, sizeof(int)) != cudaSuccess) return -1; \
+        }                                                                                            \
+        return v;                                                                                    \
+    }                                                                                                \
+    }
+#else
+#define XS_CHECK(c) true
+#define XS_CHECK_ACCESSOR(name)                 \
+    namespace xsi {                             \
+    int check_status_##name(int) { return 0; } \
+    }
+#endif
+
 __device__ __forceinline__ float rcp_fast(float x)
 {
     float r;
@@ -260,6 +295,11 @@ __device__ __forceinline__ void w_series_tab(float xh, float xl, float a, float 
     const float R4 = __expf(-4.0f * h * x);
     const float2 g = make_float2(R4, rcp_fast(R4));
     const float Rn = __expf(-4.0f * h * x * (float)n0);
+    if (!XS_CHECK(n0 >= 0 && n0 + 2 * SER_OFF < SER_TAB)) { // |z| < 6 keeps n0 <= 9
+        *wr = 0.0f;
+        *wi = 0.0f;
+        return;
+    }
     const float* d0 = dt + (n0 + SER_OFF);
     // centre term (d0[0] = 0 when n0 = 0)
     const float ep0 = E0 * Rn;

@@ -87,6 +87,7 @@ extern "C" int lines_contribution_filter(const xs_lines* lines, const double* P_
                                          double kappa_coef, double broad_scale, int32_t margin, uint8_t* keep,
                                          int32_t* n_hat, xs_stream stream)
 {
+    XS_NVTX("lines_contribution_filter");
     using namespace xsd;
     if (!lines || lines->n < 0 || !P_bar || !dP_bar || L <= 0 || !T_scan || n_scan < 1 || n_scan > FILTER_MAX_SCAN ||
         !keep)
@@ -109,3 +110,5 @@ extern "C" int lines_contribution_filter(const xs_lines* lines, const double* P_
     xsi::count_launch();
     return cudaGetLastError() == cudaSuccess ? XS_OK : XS_ECUDA;
 }
+
+XS_CHECK_ACCESSOR(filter)

@@ -2,11 +2,32 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/xs.h"
 
 namespace xsi {
+
+// NVTX range named after the library call, around its host-side work and
+// launches; costs a few nanoseconds and records nothing unless a profiler
+// (nsys, ncu's NVTX filters) is attached
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define XS_NVTX(name) ::xsi::NvtxRange xs_nvtx_range_(name)
+
+// status words of the bounds-checked build, one per translation unit with
+// kernels: the largest source line of a failed check (0: none); cleared if asked
+int check_status_linesum(int clear);
+int check_status_rt(int clear);
+int check_status_modit(int clear);
+int check_status_resp(int clear);
+int check_status_filter(int clear);
+int check_status_prior(int clear);
 
 // host-side launch counter (every kernel launch site bumps it)
 void count_launch(int n = 1);

@@ -219,7 +219,8 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
                     int64_t m = (lo + hi) >> 1;
                     if (nu[m] - nuh >= del) hi = m; else lo = m + 1;
                 }
-                const int2 cut = jrange[l];
+                int2 cut = jrange[l];
+                if (!XS_CHECK(cut.x >= 0 && cut.y < N)) cut = make_int2(1, 0);
                 r.x = (int)max((int64_t)cut.x, jl);
                 r.y = (int)min((int64_t)cut.y, lo - 1);
             }
@@ -282,23 +283,36 @@ __device__ __forceinline__ int64_t lb_jlo(const int2* jr, int64_t n, int v) // f
     return lo;
 }
 
-// Line window of a warp's points (all lines with an in-cut point in [j0, jlast])
-// and the kc-th of ksplit equal parts of it, rounded to whole 32-line chunks.
+// Line window of a warp's points (all lines with an in-cut point in [j0, jlast]),
+// and part kc of it.  Two ways to split (lb from choose_split):
+//   lb == 0: ksplit equal parts of each warp's own window, rounded to whole
+//            32-line chunks (balanced work; used when the records of the layers
+//            in flight fit in L2 anyway);
+//   lb > 0:  the kc-th absolute block [kc lb, (kc + 1) lb) of the sorted line
+//            list.  The launch grid has kc as its slowest index, so the strips
+//            and layers resident at one time all stream the same block of line
+//            records and L2 serves the re-reads of long lists.
 // Each warp takes its own window (not the strip's), so no chunk carries lines
-// that miss all of the warp's points.
-// Lane 0 searches, the warp gets the result by shuffle.
+// that miss all of the warp's points.  Lane 0 searches, the warp gets the result
+// by shuffle.
 __device__ __forceinline__ void strip_window(const int2* jrange, int64_t nl, int64_t j0, int64_t jlast, int ksplit,
-                                             int kc, int64_t* cb, int64_t* ce)
+                                             int64_t lb, int kc, int64_t* cb, int64_t* ce)
 {
     long long b = 0, e = 0;
     if ((threadIdx.x & 31) == 0) {
-        int64_t bb = lb_jhi(jrange, nl, (int)j0);
+        const int64_t bb = lb_jhi(jrange, nl, (int)j0);
         int64_t ee = lb_jlo(jrange, nl, (int)jlast);
         if (ee < bb) ee = bb;
-        int64_t per = (ee - bb + ksplit - 1) / ksplit;
-        per = (per + 31) & ~(int64_t)31;
-        b = min64(ee, bb + per * kc);
-        e = min64(ee, b + per);
+        if (lb > 0) {
+            b = bb > lb * kc ? bb : lb * kc;
+            e = ee < lb * (kc + 1) ? ee : lb * (kc + 1);
+            if (e < b) e = b;
+        } else {
+            int64_t per = (ee - bb + ksplit - 1) / ksplit;
+            per = (per + 31) & ~(int64_t)31;
+            b = min64(ee, bb + per * kc);
+            e = min64(ee, b + per);
+        }
     }
     *cb = __shfl_sync(0xffffffffu, b, 0);
     *ce = __shfl_sync(0xffffffffu, e, 0);
@@ -565,7 +579,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     const double* __restrict__ nu_hat, const float2* __restrict__ nuf, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
     const int2* __restrict__ jnear, const float* __restrict__ agg, const double* __restrict__ nu, int64_t N,
-    int64_t nl, int layer0, int ksplit, double unscale, void* __restrict__ sigma, int sigma_is_float,
+    int64_t nl, int layer0, int ksplit, int64_t lb, double unscale, void* __restrict__ sigma, int sigma_is_float,
     double* __restrict__ partial, int L_total, const double* __restrict__ near_sum)
 {
     using R4 = typename vec4<R>::type;
@@ -579,7 +593,8 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
     WarpPoints<R> pts;
     if (!pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) return;
     int64_t cb, ce;
-    strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, kc, &cb, &ce);
+    strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, lb, kc, &cb, &ce);
+    if (!XS_CHECK(cb >= 0 && cb <= ce && ce <= nl)) ce = cb;
     const int layer = layer0 + nloc;
     const float cmin = agg[4 * layer], amin = agg[4 * layer + 1], amax = agg[4 * layer + 2];
     const size_t lay = (size_t)nloc * nl; // records hold the current layer chunk
@@ -638,7 +653,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_kernel(
 
 #pragma unroll
     for (int g = 0; g < LS_G; ++g) {
-        if (pts.jg[g] <= jlast) {
+        if (pts.jg[g] <= jlast && XS_CHECK(pts.jg[g] >= 0 && pts.jg[g] < N)) {
             double v = (double)shi[g] + (double)slo[g];
             if (FAST && kc == 0) v += near_sum[(size_t)nloc * N + pts.jg[g]];
             size_t o = (size_t)layer * N + pts.jg[g];
@@ -801,43 +816,53 @@ __global__ void __launch_bounds__(NR_THREADS, 8) near_sum_kernel(const double* _
     NearTile& tl = tiles[w];
     int64_t cb, ce;
     near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
+    if (!XS_CHECK(cb >= 0 && cb <= ce && ce <= nl)) ce = cb;
     const bool live = j <= jl;
     float shi = 0.0f, slo = 0.0f;
     for (int64_t t0 = cb; t0 < ce; t0 += 32) {
         const int64_t l = t0 + lane;
         __syncwarp();
+        // stage only lines whose near range meets this warp's points
+        bool hit = false;
         if (l < ce) {
-            const double o = nu_hat[l] - ref;
-            const float bh = (float)o;
-            tl.bhi[lane] = bh;
-            tl.blo[lane] = (float)(o - (double)bh);
-            const float4 p2 = rec2[lay + l];
-            tl.r2[lane] = p2;
-            tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
-            tl.clo[lane] = clo[lay + l];
             const int2 nr = jnear[lay + l];
-            tl.jn[lane] = nr;
-            if (nr.x <= nr.y) {
+            hit = nr.x <= nr.y && nr.x <= (int)jl && nr.y >= (int)jb && XS_CHECK(nr.x >= 0 && nr.y < N);
+            if (hit) {
+                const double o = nu_hat[l] - ref;
+                const float bh = (float)o;
+                tl.bhi[lane] = bh;
+                tl.blo[lane] = (float)(o - (double)bh);
+                const float4 p2 = rec2[lay + l];
+                tl.r2[lane] = p2;
+                tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
+                tl.clo[lane] = clo[lay + l];
+                tl.jn[lane] = nr;
                 float C[ASY_N];
                 asy_coeffs(p2.y, p2.z, C);
                 store16(tl.hc[lane], C, ASY_N);
                 if (p2.y * p2.y < NEAR_POLY_Z2) series_table(p2.y, tl.sd[lane]);
             }
-        } else {
-            tl.jn[lane] = make_int2(1, 0);
         }
         __syncwarp();
-        const int nt = (int)min64(32, ce - t0);
+        // the staged lines in ascending order (warp-uniform loop)
+        unsigned m = __ballot_sync(0xffffffffu, hit);
         float acc = 0.0f;
-        for (int i = 0; i < nt; ++i) {
-            const int2 nr = tl.jn[i];
-            if (live && in_range((int)j, nr)) {
-                // x to FP32 accuracy suffices for the polynomial (a rational
-                // function of x); the series takes the exact pair
-                const float2 xa = tl.xa[i];
-                const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
-                const float z2 = fmaf(xq, xq, xa.y);
-                if (z2 >= NEAR_POLY_Z2) {
+        while (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            const bool inr = live && in_range((int)j, tl.jn[i]);
+            // x to FP32 accuracy suffices for the polynomial (a rational
+            // function of x); the series takes the exact pair
+            const float2 xa = tl.xa[i];
+            const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
+            const float z2 = fmaf(xq, xq, xa.y);
+            const bool ser = inr && z2 < NEAR_POLY_Z2;
+            if (!__any_sync(0xffffffffu, ser)) {
+                // no lane in the series zone: the polynomial, branch-free
+                const float hv = horner13(tl.hc[i], rcp_fast(z2));
+                acc += inr ? hv : 0.0f;
+            } else if (inr) {
+                if (!ser) {
                     acc += horner13(tl.hc[i], rcp_fast(z2));
                 } else {
                     const float4 p2 = tl.r2[i];
@@ -887,44 +912,55 @@ __global__ void __launch_bounds__(NR_THREADS, 6) near_adjoint_kernel(
         NearAdjTile& tl = tiles[w];
         int64_t cb, ce;
         near_window(nu_hat, nl, nu[jb], nu[jl], (double)NEAR_Z / (double)cmin * (1.0 + 1e-6), &cb, &ce);
+        if (!XS_CHECK(cb >= 0 && cb <= ce && ce <= nl)) ce = cb;
         float aT = 0.0f, aB = 0.0f;
         for (int64_t t0 = cb; t0 < ce; t0 += 32) {
             const int64_t l = t0 + lane;
             __syncwarp();
+            // stage only lines whose near range meets this warp's points
+            bool hit = false;
             if (l < ce) {
-                const double o = nu_hat[l] - ref;
-                const float bh = (float)o;
-                tl.bhi[lane] = bh;
-                tl.blo[lane] = (float)(o - (double)bh);
-                const float4 p2 = rec2[lay + l];
-                tl.r2[lane] = p2;
-                tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
-                tl.clo[lane] = clo[lay + l];
                 const int2 nr = jnear[lay + l];
-                tl.jn[lane] = nr;
-                const float aS = rec3[2 * (lay + l)], nn = rec3[2 * (lay + l) + 1];
-                tl.aS[lane] = aS;
-                tl.nn[lane] = nn;
-                if (nr.x <= nr.y) {
+                hit = nr.x <= nr.y && nr.x <= (int)jl && nr.y >= (int)jb && XS_CHECK(nr.x >= 0 && nr.y < N);
+                if (hit) {
+                    const double o = nu_hat[l] - ref;
+                    const float bh = (float)o;
+                    tl.bhi[lane] = bh;
+                    tl.blo[lane] = (float)(o - (double)bh);
+                    const float4 p2 = rec2[lay + l];
+                    tl.r2[lane] = p2;
+                    tl.xa[lane] = make_float2(-p2.x * bh, p2.y * p2.y);
+                    tl.clo[lane] = clo[lay + l];
+                    tl.jn[lane] = nr;
+                    const float aS = rec3[2 * (lay + l)], nn = rec3[2 * (lay + l) + 1];
+                    tl.aS[lane] = aS;
+                    tl.nn[lane] = nn;
                     float F[ASY_N + 1], G[ASY_N + 1];
                     asy_coeffs_adj(p2.y, p2.z, aS, half_invT, nn, F, G);
                     store16(tl.hf[lane], F, ASY_N + 1);
                     store16(tl.hg[lane], G, ASY_N + 1);
                     if (p2.y * p2.y < NEAR_POLY_Z2) series_table(p2.y, tl.sd[lane]);
                 }
-            } else {
-                tl.jn[lane] = make_int2(1, 0);
             }
             __syncwarp();
-            const int nt = (int)min64(32, ce - t0);
-            for (int i = 0; i < nt; ++i) {
-                const int2 nr = tl.jn[i];
-                if (j <= jl && in_range((int)j, nr)) {
-                    const float2 xa = tl.xa[i];
-                    const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
-                    const float z2 = fmaf(xq, xq, xa.y);
+            unsigned m = __ballot_sync(0xffffffffu, hit);
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                const bool inr = j <= jl && in_range((int)j, tl.jn[i]);
+                const float2 xa = tl.xa[i];
+                const float xq = fmaf(tl.r2[i].x, ohi, xa.x);
+                const float z2 = fmaf(xq, xq, xa.y);
+                const bool ser = inr && z2 < NEAR_POLY_Z2;
+                if (!__any_sync(0xffffffffu, ser)) {
+                    // no lane in the series zone: the polynomials, branch-free
+                    const float u = rcp_fast(z2);
+                    const float ft = horner14(tl.hf[i], u), fb = horner14(tl.hg[i], u);
+                    aT = fmaf(inr ? lam : 0.0f, inr ? ft : 0.0f, aT);
+                    aB = fmaf(inr ? lam : 0.0f, inr ? fb : 0.0f, aB);
+                } else if (inr) {
                     float ft, fb;
-                    if (z2 >= NEAR_POLY_Z2) {
+                    if (!ser) {
                         const float u = rcp_fast(z2);
                         ft = horner14(tl.hf[i], u);
                         fb = horner14(tl.hg[i], u);
@@ -1115,8 +1151,9 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     const double* __restrict__ nu_hat, const float2* __restrict__ nuf, const int2* __restrict__ jrange,
     const typename vec4<R>::type* __restrict__ rec1, const typename vec4<R>::type* __restrict__ rec2,
     const R* __restrict__ rec3, const int2* __restrict__ jnear, const float* __restrict__ agg,
-    const double* __restrict__ nu, int64_t N, int64_t nl, int layer0, int ksplit, const double* __restrict__ T,
-    const double* __restrict__ g_sigma, double lam_scale, double* __restrict__ part, int nstrips)
+    const double* __restrict__ nu, int64_t N, int64_t nl, int layer0, int ksplit, int64_t lb,
+    const double* __restrict__ T, const double* __restrict__ g_sigma, double lam_scale, double* __restrict__ part,
+    int nstrips)
 {
     using R4 = typename vec4<R>::type;
     __shared__ AdjTile<R> tiles[LS_WARPS];
@@ -1133,7 +1170,8 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     WarpPoints<R> pts;
     if (pts.init(nu, j0 + (int64_t)w * (32 * LS_G), jlast)) {
         int64_t cb, ce;
-        strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, kc, &cb, &ce);
+        strip_window(jrange, nl, pts.jw0, pts.jw1, ksplit, lb, kc, &cb, &ce);
+        if (!XS_CHECK(cb >= 0 && cb <= ce && ce <= nl)) ce = cb;
         const size_t lay = (size_t)nloc * nl;
         const R4* r1g = rec1 + lay;
         const R4* r2g = rec2 + lay;
@@ -1212,42 +1250,49 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
     }
 }
 
-// g_T[n] = sum over the main kernel's (strip, chunk) partials and the near
-// kernel's block partials; g_b = sum over layers (fixed order).
-__global__ void adjoint_reduce_kernel(const double* __restrict__ part, int L, int per_layer,
-                                      const double* __restrict__ part_near, int per_layer_near, double inv_sb,
-                                      double* __restrict__ g_T, double* __restrict__ g_b)
+// g_T[n] = sum over the main kernel's (strip, part, warp) partials and the near
+// kernel's block partials of layer n (one block per layer, fixed order);
+// gbl[n] the same for the broadening term.
+__global__ void adjoint_reduce_kernel(const double* __restrict__ part, int per_layer,
+                                      const double* __restrict__ part_near, int per_layer_near,
+                                      double* __restrict__ g_T, double* __restrict__ gbl)
 {
     __shared__ double red[2][256];
-    double gb = 0.0;
-    for (int n = 0; n < L; ++n) {
-        double a = 0.0, b = 0.0;
-        for (int i = threadIdx.x; i < per_layer; i += blockDim.x) {
-            a += part[2 * ((size_t)n * per_layer + i)];
-            b += part[2 * ((size_t)n * per_layer + i) + 1];
+    const int n = blockIdx.x;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < per_layer; i += blockDim.x) {
+        a += part[2 * ((size_t)n * per_layer + i)];
+        b += part[2 * ((size_t)n * per_layer + i) + 1];
+    }
+    if (part_near)
+        for (int i = threadIdx.x; i < per_layer_near; i += blockDim.x) {
+            a += part_near[2 * ((size_t)n * per_layer_near + i)];
+            b += part_near[2 * ((size_t)n * per_layer_near + i) + 1];
         }
-        if (part_near)
-            for (int i = threadIdx.x; i < per_layer_near; i += blockDim.x) {
-                a += part_near[2 * ((size_t)n * per_layer_near + i)];
-                b += part_near[2 * ((size_t)n * per_layer_near + i) + 1];
-            }
-        red[0][threadIdx.x] = a;
-        red[1][threadIdx.x] = b;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if (threadIdx.x < s) {
-                red[0][threadIdx.x] += red[0][threadIdx.x + s];
-                red[1][threadIdx.x] += red[1][threadIdx.x + s];
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            g_T[n] = red[0][0];
-            gb += red[1][0];
+    red[0][threadIdx.x] = a;
+    red[1][threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            red[0][threadIdx.x] += red[0][threadIdx.x + s];
+            red[1][threadIdx.x] += red[1][threadIdx.x + s];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) g_b[0] = gb * inv_sb;
+    if (threadIdx.x == 0) {
+        g_T[n] = red[0][0];
+        gbl[n] = red[1][0];
+    }
+}
+
+// g_b = sum over layers of gbl (in layer order) / s_b
+__global__ void broad_sum_kernel(const double* __restrict__ gbl, int L, double inv_sb, double* __restrict__ g_b)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int n = 0; n < L; ++n) s += gbl[n];
+        g_b[0] = s * inv_sb;
+    }
 }
 
 } // namespace xsd
@@ -1263,22 +1308,41 @@ size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
 int strips_of(int64_t N) { return (int)((N + LS_STRIP - 1) / LS_STRIP); }
 int near_blocks(int64_t N) { return (int)((N + NR_THREADS - 1) / NR_THREADS); }
 
-// split the line window of each strip so that the grid holds enough CTAs
-int choose_ksplit(int64_t nl, int64_t N, int Lc)
+// Lists whose per-layer records (about 40 bytes a line) for the layers in flight
+// (about six at four CTAs per SM) fit in 48 MB of L2 are split into equal parts of
+// each warp's window; longer ones into absolute line blocks of at most
+// LS_BLOCK_MAX lines, which keeps one block's records for the layers in flight at
+// about 16 MB, inside one die's half of the L2.
+constexpr int64_t LS_L2_LINES = 200000;
+constexpr int64_t LS_BLOCK_MAX = 65536;
+
+// Split of the line windows into ksplit parts: enough CTAs to fill the GPU
+// (several waves of 8 resident CTAs per SM); *lb = 0 for equal parts of each
+// window, else the absolute block length (a multiple of 32).
+void choose_split(int64_t nl, int64_t N, int Lc, int* ksplit, int64_t* lb)
 {
-    int strips = strips_of(N);
-    int64_t ctas = (int64_t)strips * Lc;
-    const int64_t target = 152 * 8 * 6; // several waves of 8 resident CTAs per SM
-    int k = (int)std::max<int64_t>(1, (target + ctas - 1) / ctas);
-    int64_t per_strip = std::max<int64_t>(1, nl); // upper bound of a window
-    int kmax = (int)std::max<int64_t>(1, per_strip / 1024);
-    return std::min(k, std::min(kmax, 64));
+    const int strips = strips_of(N);
+    const int64_t ctas = (int64_t)strips * Lc;
+    const int64_t target = 152 * 8 * 6;
+    int64_t k = std::max<int64_t>(1, (target + ctas - 1) / ctas);
+    if (nl <= LS_L2_LINES) {
+        *ksplit = (int)std::min<int64_t>(k, std::min<int64_t>(std::max<int64_t>(1, nl / 1024), 64));
+        *lb = 0;
+        return;
+    }
+    k = std::min<int64_t>(k, nl / 1024);
+    k = std::max<int64_t>(k, (nl + LS_BLOCK_MAX - 1) / LS_BLOCK_MAX);
+    int64_t b = (nl + k - 1) / k;
+    b = (b + 31) & ~(int64_t)31;
+    *lb = b;
+    *ksplit = (int)((nl + b - 1) / b);
 }
 
 struct XsPlan {
     int prec, Lc, ksplit, nchunks;
+    int64_t lb; // lines per block of the split
     size_t off_jr, off_nuf, off_agg, off_rec1, off_rec2, off_rec3, off_clo, off_jn, off_near, off_part, off_npart,
-        total;
+        off_gbl, total;
 };
 
 XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
@@ -1289,7 +1353,7 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
     const bool mixed = (prec == XS_PREC_MIXED);
     const size_t rs = mixed ? sizeof(float) : sizeof(double);
     const size_t n1 = (size_t)std::max<int64_t>(nl, 1);
-    p.ksplit = choose_ksplit(nl, N, Lc);
+    choose_split(nl, N, Lc, &p.ksplit, &p.lb);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -1308,6 +1372,7 @@ XsPlan plan_xs(int64_t nl, int64_t N, int32_t L, int prec, int Lc)
     size_t fwd_part = (p.ksplit > 1) ? sizeof(double) * (size_t)p.ksplit * Lc * N : 0;
     size_t adj_part = sizeof(double) * 2 * (size_t)L * strips_of(N) * p.ksplit * LS_WARPS;
     p.off_part = take(std::max(fwd_part, adj_part));
+    p.off_gbl = take(sizeof(double) * (size_t)L);
     p.off_npart = take(mixed ? sizeof(double) * 2 * (size_t)L * near_blocks(N) : 0);
     p.total = off;
     p.nchunks = (L + Lc - 1) / Lc;
@@ -1408,8 +1473,8 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
             }
             prof_begin(0, st);
             linesum_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, nuf, jr, rec1, rec2, jn, agg, nu, N, nl, l0,
-                                                                 p.ksplit, unscale, sigma, FAST ? 1 : 0, part, lc,
-                                                                 near);
+                                                                 p.ksplit, p.lb, unscale, sigma, FAST ? 1 : 0, part,
+                                                                 lc, near);
             prof_end(0, st);
             count_launch();
             if (p.ksplit > 1) {
@@ -1421,7 +1486,7 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
         } else {
             prof_begin(1, st);
             linesum_adjoint_kernel<R, FAST><<<grid, LS_THREADS, 0, st>>>(ln->nu_hat, nuf, jr, rec1, rec2, rec3, jn, agg,
-                                                                         nu, N, nl, l0, p.ksplit, T, g_sigma,
+                                                                         nu, N, nl, l0, p.ksplit, p.lb, T, g_sigma,
                                                                          unscale, part, strips);
             prof_end(1, st);
             count_launch();
@@ -1434,9 +1499,10 @@ static int run_xs(const xs_lines* ln, const double* nu, int64_t N, const double*
         }
     }
     if (adjoint) {
-        adjoint_reduce_kernel<<<1, 256, 0, st>>>(part, L, strips * p.ksplit * LS_WARPS, npart, nblk, 1.0 / sb, g_T,
-                                                  g_b);
-        count_launch();
+        double* gbl = (double*)(ws + p.off_gbl);
+        adjoint_reduce_kernel<<<L, 256, 0, st>>>(part, strips * p.ksplit * LS_WARPS, npart, nblk, g_T, gbl);
+        broad_sum_kernel<<<1, 32, 0, st>>>(gbl, L, 1.0 / sb, g_b);
+        count_launch(2);
     }
     return (cudaGetLastError() == cudaSuccess) ? XS_OK : XS_ECUDA;
 }
@@ -1468,3 +1534,5 @@ int check_sorted(const double* nu_hat, int64_t n, cudaStream_t st, int* flag_dev
 }
 
 } // namespace xsi
+
+XS_CHECK_ACCESSOR(linesum)

@@ -674,6 +674,7 @@ int modit_compute_adjoint(const xs_lines* lines, double nu_min, double nu_max, i
                           int prec, const double* g_sigma, double* g_T, double* g_broad, void* workspace,
                           size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("modit_compute_adjoint");
     if (!lines || lines->n < 0 || !T || !P_bar || !g_sigma || !g_T || !g_broad || !workspace || L <= 0 || N < 2)
         return XS_EINVAL;
     if (lines->n > 0 && (!lines->nu_hat || !lines->ln_S0 || !lines->elower || !lines->gamma_ref || !lines->n_temp))
@@ -702,6 +703,7 @@ int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N
                   const double* P_bar, int32_t L, double broad_scale, int32_t n_gamma, int64_t n_fft, int prec,
                   void* sigma, void* workspace, size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("modit_compute");
     if (!lines || lines->n < 0 || !T || !P_bar || !sigma || !workspace || L <= 0 || N < 2) return XS_EINVAL;
     if (lines->n > 0 && (!lines->nu_hat || !lines->ln_S0 || !lines->elower || !lines->gamma_ref || !lines->n_temp))
         return XS_EINVAL;
@@ -719,3 +721,5 @@ int modit_compute(const xs_lines* lines, double nu_min, double nu_max, int64_t N
 }
 
 } // extern "C"
+
+XS_CHECK_ACCESSOR(modit)

@@ -49,6 +49,7 @@ extern "C" int xs_compute_noalloc(const xs_lines* lines, const double* nu, int64
                                   const double* P_bar, int32_t L, double broad_scale, double wing_cut, int prec,
                                   void* sigma, xs_stream stream)
 {
+    XS_NVTX("xs_compute_noalloc");
     // the same argument checks as xs_compute
     int r = xsi::check_common(lines, nu, N, T, P_bar, L, broad_scale, wing_cut, prec);
     if (r) return r;

@@ -121,6 +121,7 @@ size_t gp_prior_workspace_bytes(int32_t L)
 int gp_prior_layers(const double* T, const double* P_bar, int32_t L, double T0, double a_T, double tau_P, double eps,
                     double* out, void* workspace, size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("gp_prior_layers");
     using namespace xsd;
     if (!T || !P_bar || !out || !workspace || L <= 0 || L > XS_GP_MAX_LAYERS) return XS_EINVAL;
     if (!std::isfinite(T0) || !(a_T > 0.0) || !(tau_P > 0.0) || !(eps >= 0.0)) return XS_EINVAL;
@@ -133,3 +134,5 @@ int gp_prior_layers(const double* T, const double* P_bar, int32_t L, double T0, 
 }
 
 } // extern "C"
+
+XS_CHECK_ACCESSOR(prior)

@@ -189,6 +189,7 @@ extern "C" {
 int response_rotation(const double* F0, const double* nu, int64_t N, double vsini, double u1, double u2, double* F1,
                       xs_stream stream)
 {
+    XS_NVTX("response_rotation");
     if (!F0 || !F1 || !grid_ok(nu, N) || !(vsini > 0.0) || !(1.0 - u1 / 3.0 - u2 / 6.0 > 0.0)) return XS_EINVAL;
     response_kernel<RotKernel, true><<<blocks(N), RESP_THREADS, 0, (cudaStream_t)stream>>>(
         F0, nu, N, nu, N, rot_kernel(vsini, u1, u2), 0.0, F1, nullptr, nullptr, nullptr);
@@ -198,6 +199,7 @@ int response_rotation(const double* F0, const double* nu, int64_t N, double vsin
 int response_ip_rv(const double* F1, const double* nu, int64_t N, const double* nu_out, int64_t N_out, double beta,
                    double rv, double* F, xs_stream stream)
 {
+    XS_NVTX("response_ip_rv");
     if (!F1 || !F || !grid_ok(nu, N) || !grid_ok(nu_out, N_out) || !(beta > 0.0) || !(fabs(rv) < C_KMS))
         return XS_EINVAL;
     response_kernel<GaussKernel, false><<<blocks(N_out), RESP_THREADS, 0, (cudaStream_t)stream>>>(
@@ -215,6 +217,7 @@ int response_rotation_adjoint(const double* g_F1, const double* F0, const double
                               double u1, double u2, double* g_F0, double* g_vsini, void* workspace,
                               size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("response_rotation_adjoint");
     if (!g_F1 || !F0 || !g_F0 || !g_vsini || !workspace || !grid_ok(nu, N) || !(vsini > 0.0) ||
         !(1.0 - u1 / 3.0 - u2 / 6.0 > 0.0))
         return XS_EINVAL;
@@ -234,6 +237,7 @@ int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu
                            int64_t N_out, double beta, double rv, double* g_F1, double* g_rv, void* workspace,
                            size_t workspace_bytes, xs_stream stream)
 {
+    XS_NVTX("response_ip_rv_adjoint");
     if (!g_F || !F1 || !g_F1 || !g_rv || !workspace || !grid_ok(nu, N) || !grid_ok(nu_out, N_out) ||
         !(beta > 0.0) || !(fabs(rv) < C_KMS))
         return XS_EINVAL;
@@ -251,3 +255,5 @@ int response_ip_rv_adjoint(const double* g_F, const double* F1, const double* nu
 }
 
 } // extern "C"
+
+XS_CHECK_ACCESSOR(resp)

@@ -566,3 +566,5 @@ int rt_accumulate(double* dst, const double* src, int64_t n, int first, cudaStre
 }
 
 } // namespace xsi
+
+XS_CHECK_ACCESSOR(rt)

@@ -47,12 +47,14 @@ class XsModelC(C.Structure):
 
 
 def lib():
-    """Load libxs.so (building it first if the sources are newer)."""
+    """Load libxs.so (building it first if the sources are newer); with the
+    environment variable XS_CHECKED=1, the bounds-checked build libxs_checked.so."""
     global _lib
     if _lib is None:
-        path = _build.LIB
-        if not _build.up_to_date():
-            path = _build.build()
+        checked = os.environ.get("XS_CHECKED") == "1"
+        path = _build.LIB_CHECKED if checked else _build.LIB
+        if not _build.up_to_date(checked):
+            path = _build.build(checked=checked)
         if not os.path.exists(path):
             raise RuntimeError("libxs.so is missing; run paper_2105_14782_gb300._build.build()")
         L = C.CDLL(path)
@@ -87,6 +89,7 @@ def lib():
         L.xs_profile_read.argtypes = [C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64)]
         L.xs_launch_count.restype = C.c_uint64
+        L.xs_check_status.argtypes = [i]
         L.response_rotation.argtypes = [vp, vp, i64, d, d, d, vp, vp]
         L.response_ip_rv.argtypes = [vp, vp, i64, vp, i64, d, d, vp, vp]
         L.response_workspace_bytes.restype = sz
@@ -196,12 +199,13 @@ def xs_compute_adjoint(lines: DeviceLines, nu, T, P_bar, g_sigma, broad_scale=1.
     return g_T, g_b
 
 
-def modit_fft_length(nu_min, nu_max, N, lines: "DeviceLines"):
+def modit_fft_length(nu_min, nu_max, N, lines: "DeviceLines", span=None):
     """Smallest power of two >= 2 (N + farthest centre outside the grid, in q
-    steps) + 4, so that every profile covers the whole grid."""
+    steps) + 4, so that every profile covers the whole grid.  span = (lowest,
+    highest centre), when given, replaces the read of the device list."""
     R0 = (N - 1) / math.log(nu_max / nu_min)
-    if lines.n:
-        lo, hi = float(lines.nu_hat[0].item()), float(lines.nu_hat[-1].item())
+    if span is not None or lines.n:
+        lo, hi = span if span is not None else (float(lines.nu_hat[0].item()), float(lines.nu_hat[-1].item()))
         out = max(0.0, -R0 * math.log(lo / nu_min), R0 * math.log(hi / nu_min) - (N - 1))
     else:
         out = 0.0
@@ -391,6 +395,11 @@ def profile_read():
     a, b, c, d = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
     _check("xs_profile_read", lib().xs_profile_read(C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
     return a.value, b.value, c.value, d.value
+
+
+def check_status(clear=True) -> int:
+    """0 unless a bounds check of the checked build failed (file * 100000 + line)."""
+    return int(lib().xs_check_status(int(clear)))
 
 
 def launch_count() -> int:

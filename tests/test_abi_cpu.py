@@ -127,3 +127,15 @@ def test_gp_prior_rejects_bad_arguments(lib):
         args = list(ok)
         args[k] = bad
         assert lib.gp_prior_layers(*args, None) == -1, (k, bad)
+
+
+def test_bounds_checked_build_is_marked(lib):
+    """The normal library reports no checked build and a clean status without a
+    GPU call path; the checked variant (-DXS_CHECKED) reports itself."""
+    lib.xs_checked_build.restype = C.c_int
+    assert lib.xs_checked_build() == 0
+    checked = C.CDLL(_build.build(checked=True))
+    checked.xs_checked_build.restype = C.c_int
+    assert checked.xs_checked_build() == 1
+    for n in _declared():
+        assert hasattr(checked, n), n
