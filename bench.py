@@ -41,7 +41,7 @@ import workloads as W  # noqa: E402
 T_START = time.perf_counter()
 # the whole command must end well inside the caller's limit (1,800 s): optional
 # legs are skipped, and say so, once the run gets near this budget
-WALL_BUDGET_S = 1500.0
+WALL_BUDGET_S = 1650.0
 
 FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM on sm_103a (one FFMA = 2 flops)
 
@@ -386,6 +386,8 @@ def step_bench(dev, stream, atm, prec, steps, warmup, rank, world, dist, e2e_ste
         out_h.copy_(model.out, non_blocking=True)
         F_h.copy_(model.F0, non_blocking=True)
 
+    if ms / steps > 10000.0:
+        e2e_steps = 1  # a step of tens of seconds: one end-to-end step keeps the run inside its time limit
     torch.cuda.synchronize(dev)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
@@ -463,7 +465,7 @@ def serving(dev, budget_s):
     cap = closed["evals_per_s"] / mean_ev
     slo = 4.0
     points = []
-    for frac in (0.5, 0.8):
+    for frac in (0.8, 0.5):
         need_s = 330.0 / (frac * cap) + 5.0
         if elapsed() + need_s > budget_s:
             points.append({"load_fraction": frac, "skipped": f"time budget ({need_s:.0f} s needed)"})
