@@ -3,7 +3,7 @@
 // reverse-mode adjoint.
 //
 // Partition.  For every (layer, line) the grid points inside the wing cut are
-// split, in FP64, into the line's "near" index range (|z| < 25, z = x + ia) and
+// split, in FP64, into the line's "near" index range (|z| < NEAR_Z = 16.5, z = x + ia) and
 // the rest.  The far part (about 98% of the evaluations) is summed by the main
 // kernels with the Lorentz-wing forms of the asymptotic series (Eq. asywofz) in
 // packed FP32x2 arithmetic; the near part by the near kernels, one thread per
@@ -39,8 +39,12 @@ constexpr int LS_STRIP = LS_WARPS * 32 * LS_G; // 1024
 // resident CTAs per SM the register budget targets (FP32: 96 registers; FP64 keeps more)
 template <class R> struct MinBlocks { static constexpr int v = 4; }; // 128 registers: ILP over occupancy
 template <> struct MinBlocks<double> { static constexpr int v = 3; };
-// the near/far boundary of the FP32 path: pairs at |z| < NEAR_Z go to the near kernels
-constexpr double NEAR_Z = 25.0;
+// the near/far boundary of the FP32 path: pairs at |z| < NEAR_Z go to the near
+// kernels.  At |z| >= 16.5 the K = 2 wing forms truncate the asymptotic series below
+// 1e-7 of a term (the first dropped term is 15/(8 |z|^6)); the K = 1 adjoint forms
+// are kept for |z| >= 25 (ADJ_K2_Z2) and K = 2 ones used between.
+constexpr double NEAR_Z = 16.5;
+constexpr float ADJ_K2_Z2 = 625.0f;
 
 // ------------------------------------------------------------------ K0: cut ranges
 
@@ -201,7 +205,7 @@ __global__ void line_params_kernel(const double* __restrict__ nu_hat, const doub
             rec3[2 * idx + 1] = (R)(-n_temp[l]) / Tr;
         }
         if (jnear) {
-            // near range: in-cut points with |nu_j - nu_hat| < sqrt(625 - a^2)/c, i.e. |z| < 25
+            // near range: in-cut points with |nu_j - nu_hat| < sqrt(NEAR_Z^2 - a^2)/c, i.e. |z| < NEAR_Z
             const double ad = gam * c;
             const double lim = (double)NEAR_Z * NEAR_Z - ad * ad;
             int2 r = make_int2(1, 0); // empty
@@ -479,7 +483,7 @@ __device__ __forceinline__ void chunk_far(const LineTile<float>& tl, const WarpP
         a2[p] = make_float2(acc[2 * p], acc[2 * p + 1]);
     }
     if (ok == 0xffffffffu) {
-        // every pair at |z| >= 25; K = 1 suffices when every pair is at |z| >= 100
+        // every pair at |z| >= NEAR_Z; K = 1 suffices when every pair is at |z| >= 100
         // (the K = 2 terms are below 4e-8 of the leading one), and its F2 term,
         // 2 a^2/|z|^4 of the leading one, is dropped where that is below 2e-8
         const float z2 = chunk_z2min(tl.q0[0].x, tl.q0[31].x, pts, cmin, amin);
@@ -697,7 +701,7 @@ struct NearTile {
     float4 r2[32]; // c, a, Av, Kc
     float2 xa[32]; // -c bhi, a^2: x to ~1e-7 for the wing polynomial
     int2 jn[32];
-    float4 hc[32][4]; // Av C'_0 .. Av C'_12 of the wing polynomial (6 <= |z| < 25)
+    float4 hc[32][4]; // Av C'_0 .. Av C'_12 of the wing polynomial (6 <= |z| < NEAR_Z)
     float sd[32][SER_TAB]; // series table (|z| < 6, lines with a < 6)
 };
 
@@ -707,7 +711,7 @@ struct NearAdjTile {
     float2 xa[32];
     int2 jn[32];
     float aS[32], nn[32];
-    float4 hf[32][4], hg[32][4]; // f_T and f_b wing polynomials (6 <= |z| < 25)
+    float4 hf[32][4], hg[32][4]; // f_T and f_b wing polynomials (6 <= |z| < NEAR_Z)
     float sd[32][SER_TAB];
 };
 
@@ -1024,28 +1028,63 @@ __global__ void __launch_bounds__(NR_THREADS, 6) near_adjoint_kernel(
 //   D_gamma = Al (rho + (1.5 B - 2 G) rho^2 - 12 G B rho^3 + 12 G^2 B rho^4),
 // so f_T = rho (T1 + rho (T2 + rho (T3 + rho T4))) and f_b = rho (U1 + ... U4) with
 // per-line coefficients.  At |z| >= 25 the K = 2 terms are below 6e-6 of a term.
+// With the K = 2 terms (V0 from the forward's degree-5 form, Q = B^2 Al):
+//   V0      += Q rho^3 (3.75 - 15 G rho + 12 G^2 rho^2),
+//   D_beta  += Q rho^3 (15 - 60 G rho + 48 G^2 rho^2),
+//   D_gamma += Q rho^3 (3.75 - 67.5 G rho + 180 G^2 rho^2 - 120 G^3 rho^3),
+// degree 6 in rho; used where |z| < 25 (and for the lines of a chunk that has
+// masked ones), where they truncate below 7e-7 of a term for |z| >= 16.5.
 template <class R>
 struct AdjTile {
     float4 q0[32];           // (-b, -b, G, G)
     float4 qt0[32], qt1[32]; // (T1, T1, T2, T2), (T3, T3, T4, T4)
     float4 qu0[32], qu1[32]; // (U1, U1, U2, U2), (U3, U3, U4, U4)
+    float4 qt2[32], qu2[32]; // K = 2: (T5, T5, T6, T6), (U5, U5, U6, U6)
     int2 jr[32], jn[32];
     R bhi[32];
     typename vec4<R>::type r2[32];
     R aS[32], nn[32];
 };
 
-// packed K = 1 adjoint over lines [i0, i1); MASKED: per (line, point) by far_point;
-// DEG2: the rho^3 and rho^4 terms dropped (below 1e-6 of the leading one where the
-// caller takes it).  Per point sums of f_T and f_b (lambda is applied once per
-// chunk by the caller).
-template <bool MASKED, bool DEG2 = false>
+// Turn lane's line of the tile from the K = 1 adjoint forms into the K = 2 ones.
+__device__ __forceinline__ void adj_k2_coeffs(AdjTile<float>& tl, int i, float hT)
+{
+    const float G = tl.q0[i].z, Al = tl.qu0[i].x, c = tl.r2[i].x;
+    const float aS = tl.aS[i], nn = tl.nn[i];
+    const float c2 = c * c;
+    const float Q = Al * rcp_fast(c2 * c2); // B^2 Al with B = 1/c^2
+    const float4 t1 = tl.qt1[i], u1 = tl.qu1[i];
+    const float GQ = G * Q, G2Q = G * GQ;
+    const float T3 = fmaf(Q, 3.75f * aS + 15.0f * hT + 3.75f * nn, t1.x);
+    const float T4 = fmaf(-GQ, 15.0f * aS + 60.0f * hT + 67.5f * nn, t1.z);
+    const float T5 = G2Q * (12.0f * aS + 48.0f * hT + 180.0f * nn);
+    const float T6 = -120.0f * G * G2Q * nn;
+    const float U3 = fmaf(3.75f, Q, u1.x), U4 = fmaf(-67.5f, GQ, u1.z);
+    const float U5 = 180.0f * G2Q, U6 = -120.0f * G * G2Q;
+    tl.qt1[i] = make_float4(T3, T3, T4, T4);
+    tl.qu1[i] = make_float4(U3, U3, U4, U4);
+    tl.qt2[i] = make_float4(T5, T5, T6, T6);
+    tl.qu2[i] = make_float4(U5, U5, U6, U6);
+}
+
+// packed adjoint over lines [i0, i1); MASKED: per (line, point) by far_point;
+// DEG2: the K = 1 forms with the rho^3 and rho^4 terms dropped (below 1e-6 of the
+// leading one where the caller takes it); K2: the degree-6 K = 2 forms (after
+// adj_k2_coeffs); otherwise the K = 1 forms.  Per point sums of f_T and f_b (lambda
+// is applied once per chunk by the caller).
+template <bool MASKED, bool DEG2 = false, bool K2 = false>
 __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, int i1, const float2 (&o2)[LS_G / 2],
                                               float2 (&aT)[LS_G / 2], float2 (&aB)[LS_G / 2], const int (&jg)[LS_G])
 {
-#pragma unroll 4
+    constexpr int UNROLL = K2 ? 2 : 4; // the longer K = 2 forms keep fewer lines in flight
+#pragma unroll UNROLL
     for (int i = i0; i < i1; ++i) {
         const float4 v0 = tl.q0[i], t0 = tl.qt0[i], t1 = tl.qt1[i], u0 = tl.qu0[i], u1 = tl.qu1[i];
+        float4 t2 = make_float4(0.f, 0.f, 0.f, 0.f), u2 = t2;
+        if (K2) {
+            t2 = tl.qt2[i];
+            u2 = tl.qu2[i];
+        }
         const float2 nb = f2lo(v0), G = f2hi(v0);
         int2 cut = make_int2(0, 0), nr = make_int2(1, 0);
         if (MASKED) {
@@ -1060,6 +1099,11 @@ __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, 
             if (DEG2) {
                 pt = __ffma2_rn(f2hi(t0), rho, f2lo(t0));
                 pu = __ffma2_rn(f2hi(u0), rho, f2lo(u0));
+            } else if (K2) {
+                pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t2), rho, f2lo(t2)), rho, f2hi(t1)),
+                                                                 rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
+                pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u2), rho, f2lo(u2)), rho, f2hi(u1)),
+                                                                 rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
             } else {
                 pt = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(t1), rho, f2lo(t1)), rho, f2hi(t0)), rho, f2lo(t0));
                 pu = __ffma2_rn(__ffma2_rn(__ffma2_rn(f2hi(u1), rho, f2lo(u1)), rho, f2hi(u0)), rho, f2lo(u0));
@@ -1074,8 +1118,8 @@ __device__ __forceinline__ void far_adj_lines(const AdjTile<float>& tl, int i0, 
     }
 }
 
-__device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const WarpPoints<float>& pts,
-                                              const float (&lam)[LS_G], float cmin, float amin, float amax,
+__device__ __forceinline__ void chunk_far_adj(AdjTile<float>& tl, const WarpPoints<float>& pts,
+                                              const float (&lam)[LS_G], float cmin, float amin, float amax, float hT,
                                               float& accT, float& accB)
 {
     const int lane = threadIdx.x & 31;
@@ -1089,23 +1133,33 @@ __device__ __forceinline__ void chunk_far_adj(const AdjTile<float>& tl, const Wa
     }
     if (ok == 0xffffffffu) {
         // the rho^3 and rho^4 terms of f_T and f_b come from the F2 term (relative
-        // size up to 12 a^2/|z|^4): dropped where that is below 1e-6
+        // size up to 12 a^2/|z|^4): dropped where that is below 1e-6; below |z| = 25
+        // the K = 2 terms are kept
         const float z2 = chunk_z2min(tl.q0[0].x, tl.q0[31].x, pts, cmin, amin);
-        if (12.0f * amax * amax <= 1.0e-6f * z2 * z2)
+        if (z2 < ADJ_K2_Z2) {
+            adj_k2_coeffs(tl, lane, hT);
+            __syncwarp();
+            far_adj_lines<false, false, true>(tl, 0, 32, o2, aT, aB, pts.jg);
+        } else if (12.0f * amax * amax <= 1.0e-6f * z2 * z2) {
             far_adj_lines<false, true>(tl, 0, 32, o2, aT, aB, pts.jg);
-        else
+        } else {
             far_adj_lines<false>(tl, 0, 32, o2, aT, aB, pts.jg);
+        }
     } else {
+        // a chunk with lines that cover the warp's points only in part: K = 2 forms
+        // throughout (its far pairs reach down to the near boundary)
+        adj_k2_coeffs(tl, lane, hT);
+        __syncwarp();
         int i = 0;
         while (i < 32) {
             const unsigned rest = ok >> i;
             if (rest & 1u) {
                 const unsigned zeros = ~rest;
                 const int j = (zeros == 0u) ? 32 : i + __ffs(zeros) - 1;
-                far_adj_lines<false>(tl, i, j, o2, aT, aB, pts.jg);
+                far_adj_lines<false, false, true>(tl, i, j, o2, aT, aB, pts.jg);
                 i = j;
             } else {
-                far_adj_lines<true>(tl, i, i + 1, o2, aT, aB, pts.jg);
+                far_adj_lines<true, false, true>(tl, i, i + 1, o2, aT, aB, pts.jg);
                 ++i;
             }
         }
@@ -1227,7 +1281,7 @@ __global__ void __launch_bounds__(LS_THREADS, MinBlocks<R>::v) linesum_adjoint_k
                 nnn = (l < ce) ? r3g[2 * l + 1] : R(0);
             }
             if constexpr (FAST)
-                chunk_far_adj(tl, pts, lam, cmin, amin, amax, accT, accB);
+                chunk_far_adj(tl, pts, lam, cmin, amin, amax, (float)half_invT, accT, accB);
             else
                 chunk_fp64_adj(tl, pts, lam, half_invT, accT, accB);
             sT += (double)accT;
