@@ -52,13 +52,13 @@ FP32_LANES_PER_SM = 128  # FP32 FMA lanes per SM on sm_103a (one FFMA = 2 flops)
 # sources they were taken on (the hash); otherwise the bench falls back to the
 # cheapest-form lower bound and says so.
 FLOPS_PER_TRIPLE = {
-    "sources_sha256": "1adb515d4722687e46cdb750c15fbfdfcaece8f86aad247126ce0df0749e4784",
-    "scale": {"fwd": 9.00, "adj": 13.01,
+    "sources_sha256": "bcfd701beb7a1f40c608e700fbcde5e1301ffb6eae228c6aed4523b1b23de8d7",
+    "scale": {"fwd": 9.00, "adj": 13.21,
               "capture": "both species' launches of a 5-layer slice of the 10.2M-line workload (10,000,000 + "
-                         "200,000 lines, 100,000 points): 3.44e13 and 4.98e13 FP32 flops over 3.82e12 triples"},
-    "emission": {"fwd": 9.16, "adj": 12.96,
+                         "200,000 lines, 100,000 points): 3.44e13 and 5.05e13 FP32 flops over 3.82e12 triples"},
+    "emission": {"fwd": 9.16, "adj": 13.38,
                  "capture": "both species' launches of a 20-layer slice of the emission workload (200,000 + 20,000 "
-                            "lines, 20,000 points): 6.05e11 and 8.56e11 FP32 flops over 6.60e10 triples"},
+                            "lines, 20,000 points): 6.05e11 and 8.84e11 FP32 flops over 6.60e10 triples"},
 }
 FLOPS_LOWER_BOUND = {"fwd": 8, "adj": 12}  # cheapest packed wing forms, RCP counted as 1 flop
 
@@ -67,9 +67,9 @@ FLOPS_LOWER_BOUND = {"fwd": 8, "adj": 12}  # cheapest packed wing forms, RCP cou
 # slices (the traffic is per layer: each layer's records are read once from DRAM
 # when L2 serves the re-reads); null unless the sources still hash to the captured ones.
 TRAFFIC = {
-    "sources_sha256": "1adb515d4722687e46cdb750c15fbfdfcaece8f86aad247126ce0df0749e4784",
-    "scale": {"fwd": 2.995e8, "adj": 3.137e8},
-    "emission": {"fwd": 3.03e7, "adj": 5.81e7},
+    "sources_sha256": "bcfd701beb7a1f40c608e700fbcde5e1301ffb6eae228c6aed4523b1b23de8d7",
+    "scale": {"fwd": 2.992e8, "adj": 3.132e8},
+    "emission": {"fwd": 3.04e7, "adj": 5.76e7},
     "capture": "ncu dram__bytes_read.sum + dram__bytes_write.sum of both species' launches, 5-layer slice of the "
                "10.2M-line workload and 20-layer slice of the emission workload, scaled to the launch's layers",
 }
