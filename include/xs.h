@@ -399,14 +399,15 @@ int xs_model_logl_grad_layers(const xs_model* model, const double* T, const doub
  *   out [L + 2] device doubles: log p(T) (normalised density, with -(L/2) log 2 pi),
  *       d log p / dT_n for every layer, d log p / dT0
  * FP64 Cholesky factorisation of K in the workspace (gp_prior_workspace_bytes(L):
- * L^2 + L doubles, caller-owned), one CTA, stream-ordered.  A K that is not
+ * L^2 + L doubles, caller-owned), one CTA (O(L^3 / 6) work; milliseconds at the
+ * paper's 100 layers), stream-ordered.  A K that is not
  * positive definite in FP64 gives NaN in out[0] and out[L + 1].  XS_EINVAL for
  * null pointers, L out of range, a_T <= 0, tau_P <= 0, eps < 0, a non-finite T0
  * or a short workspace; XS_ECUDA on launch failure.  The posterior of the
  * layer-by-layer retrieval is xs_model_logl_grad_layers' logL plus this log p,
  * and its gradient in T_n the sum of the two.
  */
-#define XS_GP_MAX_LAYERS 4096
+#define XS_GP_MAX_LAYERS 1024
 size_t gp_prior_workspace_bytes(int32_t L);
 int gp_prior_layers(const double* T, const double* P_bar, int32_t L, double T0, double a_T, double tau_P, double eps,
                     double* out, void* workspace, size_t workspace_bytes, xs_stream stream);

@@ -117,13 +117,13 @@ def test_gp_prior_rejects_bad_arguments(lib):
     lib.gp_prior_workspace_bytes.argtypes = [C.c_int32]
     assert lib.gp_prior_workspace_bytes(100) == 8 * (100 * 100 + 100)
     assert lib.gp_prior_workspace_bytes(0) == 0
-    assert lib.gp_prior_workspace_bytes(5000) == 0
+    assert lib.gp_prior_workspace_bytes(1025) == 0
     vp, d = C.c_void_p, C.c_double
     lib.gp_prior_layers.argtypes = [vp, vp, C.c_int32, d, d, d, d, vp, vp, C.c_size_t, vp]
     buf = (C.c_double * 16)()
     p = C.cast(buf, vp)
     ok = (p, p, 2, 1300.0, 1e6, 3.0, 1e-5, p, p, 8 * 6)
-    for k, bad in ((0, None), (2, 0), (2, 5000), (3, float("nan")), (4, 0.0), (5, -1.0), (6, -1e-5), (9, 8 * 5)):
+    for k, bad in ((0, None), (2, 0), (2, 1025), (3, float("nan")), (4, 0.0), (5, -1.0), (6, -1e-5), (9, 8 * 5)):
         args = list(ok)
         args[k] = bad
         assert lib.gp_prior_layers(*args, None) == -1, (k, bad)
