@@ -31,7 +31,8 @@ def _rank(rank, world, port, out):
 
 def test_two_replicas_take_the_slowest_rank():
     world = 2
-    out = mp.Manager().dict()
+    # spawn, not fork: this process already runs torch's threads
+    out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
     for r in range(world):
         t, v = out[r]
