@@ -314,10 +314,13 @@ int xs_model_logl_grad(const xs_model* model, const double* theta, double* out, 
  *     axis; subtracting it removes the Lorentz aliasing to first order in
  *     gamma'/n_fft (the paper names an aliasing correction without stating it).
  * No wing cut: each profile reaches half the period n_fft on either side.
- * Limitation: for Lorentz widths of hundreds of q steps (deep layers on coarse
- * grids) the first-order image correction leaves ringing of a few 1e-3 of the
- * layer maximum, so sigma can go negative there; check sigma >= 0 before using
- * MODIT cross-sections in an optical depth.  n_fft
+ * Resolution: the Gaussian factor is applied only up to the Nyquist frequency of
+ * the q grid, so the grid must resolve the Doppler width (Sec. 4: R0 >~ 5e5).
+ * With beta' below about one q step (cool upper layers on grids coarser than the
+ * Doppler width) the cut transform rings and sigma goes negative near lines, by
+ * up to a few 1e-2 of the layer maximum; with beta' >= 1.5 in every layer it
+ * stays non-negative on the workloads tested.  The call does not check this.
+ * n_fft
  * (a power of two, >= N + 2) is the padded period; for profiles that cover the
  * whole grid use n_fft >= 2 (N + m), m the farthest centre outside the grid in q
  * steps.  Lines whose centre lies more than (n_fft - N)/2 q steps outside the grid

@@ -10,7 +10,8 @@ several requests overlaps on the GPU.  Completion is detected by polling CUDA
 events; every wait is bounded.
 
 The scheduling core (Arena, Scheduler) is plain host code and runs with any
-executor; `LibxsExecutor` launches the work through libxs (xs_model_logl_grad).
+executor; `LibxsExecutor` launches the work through libxs (xs_model_logl_grad),
+with the direct line sum or, per request, MODIT.
 """
 from __future__ import annotations
 
@@ -27,6 +28,27 @@ import numpy as np
 import workloads as W
 
 ALIGN = 256
+
+# MODIT (Sec. 2.1.2) multiplies by the Gaussian's transform only up to the Nyquist
+# frequency of the q grid, so the grid must resolve the Doppler width (Sec. 4 asks
+# for R0 >~ 5e5 to resolve the line profile).  Below about one q step the cut
+# transform rings and the cross-section goes negative near lines, which an optical
+# depth cannot take.  A MODIT request is admitted only when beta', the Doppler
+# width in q steps, is at least this for every species in the coolest layer.
+MODIT_MIN_BETA_Q = 1.5
+_KB, _AMU, _C = 1.380649e-16, 1.66053906660e-24, 2.99792458e10  # cgs
+
+
+def modit_beta_q(n_grid, T, mass_amu, nu_min=W.NU_MIN, nu_max=W.NU_MAX):
+    """beta' = R0 sqrt(kB T/(M m_u))/c (Sec. 2.1.2), the Doppler width in steps
+    of q = R0 ln nu, R0 = (N - 1)/ln(nu_max/nu_min), on an N-point log grid."""
+    R0 = (n_grid - 1) / math.log(nu_max / nu_min)
+    return R0 * math.sqrt(_KB * T / (mass_amu * _AMU)) / _C
+
+
+def coolest_layer_T(theta, p_bar):
+    """Smallest layer temperature of the power law T0 P^alpha (Sec. 5.2)."""
+    return float(np.min(float(theta[0]) * np.asarray(p_bar, dtype=np.float64) ** float(theta[1])))
 
 # request status
 PENDING, RUNNING, DONE, REJECTED, FAILED, CANCELLED = "pending", "running", "done", "rejected", "failed", "cancelled"
@@ -84,6 +106,7 @@ class Request:
     n_grid: int
     n_layers: int
     theta: np.ndarray
+    method: str = "lpf"  # cross-section: "lpf" (direct line sum) or "modit"
     t_submit: float = 0.0
     t_start: float = 0.0
     t_done: float = 0.0
@@ -119,7 +142,11 @@ class Scheduler:
         req.nbytes = self.ex.bytes_needed(req)
         if req.nbytes <= 0 or req.nbytes > self.arena.size or not self.ex.valid(req):
             req.status = REJECTED
-            req.error = "invalid request" if req.nbytes <= 0 or not self.ex.valid(req) else "exceeds device budget"
+            if req.nbytes <= 0 or not self.ex.valid(req):
+                why = getattr(self.ex, "invalid_reason", None)
+                req.error = (why(req) if why is not None else "") or "invalid request"
+            else:
+                req.error = "exceeds device budget"
             req.t_done = req.t_submit
             self.counts["rejected"] += 1
             self.done.append(req)
@@ -217,6 +244,9 @@ class LinePool:
         co = W.co_like(2000, seed=seed + 100)
         self.lists = {n: xs.DeviceLines(h, device) for n, h in hosts.items()}
         self.co = xs.DeviceLines(co, device)
+        # lowest and highest centre of each list (MODIT's padded period), from the host copies
+        self.spans = {n: (float(np.min(h.nu_hat)), float(np.max(h.nu_hat))) for n, h in hosts.items()}
+        self.co_span = (float(np.min(co.nu_hat)), float(np.max(co.nu_hat)))
         # sum over lines of the fraction of a full-band log grid inside each line's
         # wing cut: in-cut pairs of an N-point grid ~ fraction * N (for reporting)
         ref = W.grid_lognu(200_001)
@@ -234,9 +264,10 @@ class LinePool:
 
 class LibxsExecutor:
     """Runs a request as xs_model_logl_grad on its slot's stream, inside its arena
-    block: [model workspace | grid | P | dP | d_obs | sig_obs | out]."""
+    block: [model workspace | grid | P | dP | d_obs | sig_obs | out].  A request
+    with method "modit" takes the MODIT cross-section (n_gamma width nodes)."""
 
-    def __init__(self, pool: LinePool, arena_tensor, streams, prec=1, fail_hook=None):
+    def __init__(self, pool: LinePool, arena_tensor, streams, prec=1, fail_hook=None, n_gamma=16):
         import torch
         from . import xs
         self.torch, self.xs = torch, xs
@@ -246,6 +277,7 @@ class LibxsExecutor:
         self.streams = streams
         self.prec = prec
         self.fail_hook = fail_hook
+        self.n_gamma = int(n_gamma)
         self.lib = xs.lib()
         # per-slot pinned host staging, allocated once (grown only for a larger
         # request): a slot's next request starts after its previous one completed,
@@ -261,18 +293,44 @@ class LibxsExecutor:
             self.stage[slot] = buf
         return buf
 
+    def invalid_reason(self, r):
+        """Why the request cannot run ("" when it can)."""
+        if not (r.n_lines >= 1 and 2 <= r.n_grid <= 2_000_000 and 1 <= r.n_layers <= 1000
+                and np.all(np.isfinite(r.theta))):
+            return "invalid request"
+        if r.method not in ("lpf", "modit"):
+            return f"unknown method {r.method!r}"
+        if r.method == "modit":
+            T_min = coolest_layer_T(r.theta, W.pressure_layers(r.n_layers)[0])
+            mass = max(l.mass_amu for l in self._lines(r))
+            bq = modit_beta_q(r.n_grid, T_min, mass)
+            if not bq >= MODIT_MIN_BETA_Q:
+                return (f"grid too coarse for MODIT: Doppler width {bq:.2f} q steps at {T_min:.0f} K "
+                        f"(needs {MODIT_MIN_BETA_Q})")
+        return ""
+
     def valid(self, r):
-        return r.n_lines >= 1 and 2 <= r.n_grid <= 2_000_000 and 1 <= r.n_layers <= 1000 and np.all(np.isfinite(r.theta))
+        return self.invalid_reason(r) == ""
+
+    def _lines(self, r):
+        return [self.pool.lists[self.pool.nearest(r.n_lines)], self.pool.co]
 
     def _model(self, r, ptrs=None):
         xs = self.xs
-        lines = [self.pool.lists[self.pool.nearest(r.n_lines)], self.pool.co]
         sp = (xs.XsLinesC * xs.MAX_SPECIES)()
-        for i, s in enumerate(lines):
+        for i, s in enumerate(self._lines(r)):
             sp[i] = s.struct()
         p = ptrs or {}
-        return xs.XsModelC(2, sp, p.get("nu"), r.n_grid, p.get("P"), p.get("dP"), r.n_layers, 25.0, 1e5, 2.313, 1e-8,
-                           p.get("d"), p.get("s"), self.prec)
+        m = xs.XsModelC(2, sp, p.get("nu"), r.n_grid, p.get("P"), p.get("dP"), r.n_layers, 25.0, 1e5, 2.313, 1e-8,
+                        p.get("d"), p.get("s"), self.prec)
+        if r.method == "modit":
+            nu = W.grid_lognu(r.n_grid)  # the request's grid, whose ends MODIT's q axis takes
+            nu0, nu1 = float(nu[0]), float(nu[-1])
+            m.method, m.n_gamma, m.nu_min, m.nu_max = 1, self.n_gamma, nu0, nu1
+            spans = (self.pool.spans[self.pool.nearest(r.n_lines)], self.pool.co_span)
+            for i, (lines, span) in enumerate(zip(self._lines(r), spans)):
+                m.n_fft[i] = xs.modit_fft_length(nu0, nu1, r.n_grid, lines, span=span)
+        return m
 
     def _layout(self, r):
         # sizing only: the model check wants non-null buffers, any device address will do
@@ -325,7 +383,9 @@ class LibxsExecutor:
             out_h.copy_(self.arena_t.narrow(0, off0 + lay["out"][0], 48).view(torch.float64), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        r.evals = 2 * L * (self.pool.cut_fraction(self.pool.nearest(r.n_lines)) * N + self.pool.co_fraction * N)
+        # Voigt evaluations of the line sum (forward and adjoint); MODIT evaluates none
+        r.evals = 0 if r.method == "modit" else \
+            2 * L * (self.pool.cut_fraction(self.pool.nearest(r.n_lines)) * N + self.pool.co_fraction * N)
         return (ev, out_h, host)
 
     def ready(self, r):
@@ -450,10 +510,10 @@ def summarize(finished, wall_s):
             "mean_s": float(np.mean(lat)), "wall_s": wall_s}
 
 
-def make_server(arena_bytes=int(40e9), slots=4, prec=1, device="cuda", fail_hook=None, pool=None):
+def make_server(arena_bytes=int(40e9), slots=4, prec=1, device="cuda", fail_hook=None, pool=None, n_gamma=16):
     import torch
     pool = pool or LinePool(device)
     arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
     streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
-    ex = LibxsExecutor(pool, arena, streams, prec=prec, fail_hook=fail_hook)
+    ex = LibxsExecutor(pool, arena, streams, prec=prec, fail_hook=fail_hook, n_gamma=n_gamma)
     return Scheduler(ex, int(arena_bytes), slots), pool

@@ -74,3 +74,29 @@ def test_oversized_request_rejected_others_served(pool):
     s.drain(timeout_s=120)
     assert big.status == serve.REJECTED
     assert all(r.status == serve.DONE for r in reqs)
+
+
+def test_modit_requests_beside_line_sum_requests(pool):
+    """MODIT requests on grids that resolve the Doppler width run in the mix with
+    line-sum requests and equal the direct MODIT model call; a MODIT request on a
+    grid coarser than the Doppler width is rejected with the reason."""
+    from paper_2105_14782_gb300 import serve, xs
+    th = np.array([1300.0, 0.1, -3.5, -3.0, 1.0])  # coolest layer 651 K
+    fine = [serve.Request(rid=100 + i, chain=i, n_lines=n, n_grid=g, n_layers=30, theta=th, method="modit")
+            for i, (n, g) in enumerate([(3000, 20_000), (1000, 30_000)])]
+    coarse = serve.Request(rid=200, chain=9, n_lines=1000, n_grid=3000, n_layers=30, theta=th, method="modit")
+    lpf = _requests(4)
+    s, _ = serve.make_server(arena_bytes=4 << 30, slots=4, pool=pool, n_gamma=16)
+    for r in fine + [coarse] + lpf:
+        s.submit(r)
+    s.drain(timeout_s=300)
+    assert coarse.status == serve.REJECTED and "too coarse for MODIT" in coarse.error, coarse.error
+    for r in fine + lpf:
+        assert r.status == serve.DONE, r.error
+    for r in fine:
+        P, dP = W.pressure_layers(r.n_layers)
+        atm = W.Atmosphere(species=[], vmr=[], nu=W.grid_lognu(r.n_grid), p_bar=P, dp_bar=dP)
+        m = xs.EmissionModel(atm, prec=xs.PREC_MIXED, lines=[pool.lists[pool.nearest(r.n_lines)], pool.co],
+                             d_obs=np.ones(r.n_grid), sig_obs=np.full(r.n_grid, 0.01), method="modit", n_gamma=16)
+        logl, g = m.logl_grad(r.theta)
+        np.testing.assert_array_equal(r.result, np.concatenate([[logl], g]))

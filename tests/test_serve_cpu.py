@@ -177,3 +177,62 @@ def test_open_loop_drains_and_counts_all_arrivals():
     assert len(sent) > 5 and all(r.status == serve.DONE for r in sent)
     st = serve.summarize(sent, wall)
     assert st["completed"] == len(sent) and st["p99_s"] >= st["p50_s"]
+
+
+class ReasonExecutor(FakeExecutor):
+    def invalid_reason(self, r):
+        return "" if r.n_grid > 0 else "grid too coarse for MODIT: test"
+
+    def valid(self, r):
+        return self.invalid_reason(r) == ""
+
+
+def test_rejection_carries_the_executors_reason():
+    clk = FakeClock()
+    s = serve.Scheduler(ReasonExecutor(clk), arena_bytes=100_000, slots=1, clock=clk)
+    bad = s.submit(req(0, ng=0))
+    assert bad.status == serve.REJECTED and bad.error == "grid too coarse for MODIT: test"
+
+
+def test_modit_doppler_width_in_q_steps_matches_the_oracle():
+    """beta' = R0 beta/nu_hat (Sec. 2.1.2) from the oracle's per-line Doppler widths
+    equals the serving rule's closed form for both species, at any line."""
+    oracle = pytest.importorskip("oracle")
+    import workloads as W
+    N, T = 12_000, 651.0
+    R0 = (N - 1) / np.log(W.NU_MAX / W.NU_MIN)
+    for lines in (W.water_like(50, seed=5), W.co_like(50, seed=6)):
+        _, beta, _ = oracle.line_params(lines, T, 1.0)
+        bq = R0 * np.asarray(beta).ravel() / lines.nu_hat
+        np.testing.assert_allclose(bq, serve.modit_beta_q(N, T, lines.mass_amu), rtol=1e-12)
+
+
+def test_coolest_layer_matches_the_oracle_profile():
+    oracle = pytest.importorskip("oracle")
+    import workloads as W
+    P = W.pressure_layers(30)[0]
+    for th in ((1300.0, 0.1), (1000.0, 0.2), (1600.0, 0.05)):
+        assert serve.coolest_layer_T(th, P) == pytest.approx(float(np.min(oracle.temperatures(th[0], th[1], P))),
+                                                             rel=1e-14)
+
+
+def test_modit_rule_separates_negative_from_nonnegative_cross_sections():
+    """The oracle's MODIT cross-section goes negative near lines when the grid is
+    coarser than the Doppler width, and stays non-negative in every layer once the
+    rule (beta' >= MODIT_MIN_BETA_Q in the coolest layer) admits the grid."""
+    oracle = pytest.importorskip("oracle")
+    import workloads as W
+    P = W.pressure_layers(30)[0]
+    th = (1300.0, 0.1)
+    T = oracle.temperatures(th[0], th[1], P)
+    t_min = serve.coolest_layer_T(th, P)
+    species = ((W.water_like(300, seed=5), 18.0), (W.co_like(100, seed=6), 28.0))
+    for N, admitted in ((3000, False), (8000, False), (12_000, True), (16_000, True)):
+        nu = W.grid_lognu(N)
+        bq = min(serve.modit_beta_q(N, t_min, m) for _, m in species)
+        assert (bq >= serve.MODIT_MIN_BETA_Q) == admitted
+        lo = min(float(np.min(oracle.modit(ll, nu[0], nu[-1], N, T, P, 1.0, n_gamma=16))) for ll, _ in species)
+        if admitted:
+            assert lo >= 0.0
+        elif N == 3000:
+            assert lo < 0.0
