@@ -457,8 +457,8 @@ def serving(dev, budget_s):
     offered; line count log-uniform 1e3..1e6, grid 2,000..50,000, layers 20..200):
     a saturated closed loop (the saturation point), then open-loop Poisson
     arrivals at two fractions of the capacity it measured, each until at least
-    300 requests have completed, with latency binned by request size, and the
-    FP64 path on a bounded sample of the same stream."""
+    300 requests have completed, with latency binned by request size, the FP64
+    path on a bounded sample of the same stream, and a burst of MODIT requests."""
     import torch
     from paper_2105_14782_gb300 import serve, xs
 
@@ -510,18 +510,51 @@ def serving(dev, budget_s):
         res[prec] = (sum(r.evals for r in reqs) / dt, [r.latency for r in reqs])
     e64, lat64 = res[xs.PREC_FP64]
     emx, latmx = res[xs.PREC_MIXED]
+    modit = None
+    if elapsed() + 60.0 < budget_s:
+        try:
+            modit = modit_burst(sched, arena_bytes, slots)
+        except Exception as e:  # reported, not fatal to the line
+            modit = {"error": f"{type(e).__name__}: {e}"}
     fp64 = {"evals_per_s": e64, "capacity_req_per_s": e64 / mean_ev, "latency_s": lat64,
             "mixed_evals_per_s_same_requests": emx, "mixed_latency_s": latmx,
             "sample": f"{len(sample)} requests of the stream with <= 2e10 evaluations each, run one at a time"}
     del sched, pool
     torch.cuda.empty_cache()
     return {"slo_p99_s": slo, "open_loop": points, "closed_loop_saturation": closed, "capacity_req_per_s": cap,
-            "mean_request_evals": mean_ev, "fp64_path": fp64, "slots": slots, "arena_bytes": arena_bytes,
+            "mean_request_evals": mean_ev, "fp64_path": fp64, "modit_burst": modit, "slots": slots,
+            "arena_bytes": arena_bytes,
             "setup_s": setup_s,
             "requests": "line count log-uniform 1e3..1e6 (served by the nearest of 7 resident water-like lists "
                         "1e3..1e6 plus 2,000 CO-like lines), grid 2,000..50,000, layers 20..200; "
                         "fwd + grad (logL, dlogL/dtheta), FP32 Voigt with FP64 offsets",
             "latency": "submit to result on the host (pinned D2H of logL and gradient done)"}
+
+
+def modit_burst(sched, arena_bytes, slots, n=100):
+    """n requests of the serving stream asking for MODIT, submitted at once to a
+    server with the same executor; those whose grid does not resolve the Doppler
+    width are rejected at admission.  Latencies of the completed ones."""
+    from paper_2105_14782_gb300 import serve
+    s3 = serve.Scheduler(sched.ex, arena_bytes, slots)
+    mreqs = serve.request_stream(n, seed=W.SEED_SERVE + 60)
+    t0 = time.perf_counter()
+    for r in mreqs:
+        r.method = "modit"
+        s3.submit(r)
+    s3.drain(timeout_s=600)
+    wall = time.perf_counter() - t0
+    ok = [r for r in mreqs if r.status == serve.DONE]
+    lat = np.array([r.latency for r in ok]) if ok else np.zeros(1)
+    return {"submitted": len(mreqs), "completed": len(ok),
+            "rejected_coarse_grid": sum(r.status == serve.REJECTED and "too coarse" in r.error for r in mreqs),
+            "rejected_other": sum(r.status == serve.REJECTED and "too coarse" not in r.error for r in mreqs),
+            "failed": sum(r.status == serve.FAILED for r in mreqs), "wall_s": wall,
+            "req_per_s": len(ok) / wall, "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "grid_points_completed": [min((r.n_grid for r in ok), default=0), max((r.n_grid for r in ok), default=0)],
+            "rule": f"beta' >= {serve.MODIT_MIN_BETA_Q} q steps for every species in the coolest layer",
+            "n_gamma": sched.ex.n_gamma,
+            "latency": "all submitted at once: latencies include queueing behind the burst"}
 
 
 def modit_stats(dev, atm):
