@@ -466,7 +466,8 @@ def serving(dev, budget_s):
     pool = serve.LinePool(dev)
     mean_ev = serve.mean_request_evals(pool)
     arena_bytes, slots = 64 << 30, 4
-    sched, _ = serve.make_server(arena_bytes=arena_bytes, slots=slots, pool=pool, device=dev)
+    sched, _ = serve.make_server(arena_bytes=arena_bytes, slots=slots, pool=pool, device=dev, priority=True,
+                                 hi_evals=1e11)
     warm = serve.request_stream(8, seed=W.SEED_SERVE + 50)
     for r in warm:
         r.n_lines, r.n_grid = 1000, 2000
@@ -525,6 +526,7 @@ def serving(dev, budget_s):
             "mean_request_evals": mean_ev, "fp64_path": fp64, "modit_burst": modit, "slots": slots,
             "arena_bytes": arena_bytes,
             "setup_s": setup_s,
+            "priority": "line-sum requests under 1e11 evaluations run on high-priority streams",
             "requests": "line count log-uniform 1e3..1e6 (served by the nearest of 7 resident water-like lists "
                         "1e3..1e6 plus 2,000 CO-like lines), grid 2,000..50,000, layers 20..200; "
                         "fwd + grad (logL, dlogL/dtheta), FP32 Voigt with FP64 offsets",

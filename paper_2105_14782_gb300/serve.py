@@ -107,6 +107,7 @@ class Request:
     n_layers: int
     theta: np.ndarray
     method: str = "lpf"  # cross-section: "lpf" (direct line sum) or "modit"
+    high_priority: bool = False  # ran on its slot's high-priority stream
     t_submit: float = 0.0
     t_start: float = 0.0
     t_done: float = 0.0
@@ -265,9 +266,13 @@ class LinePool:
 class LibxsExecutor:
     """Runs a request as xs_model_logl_grad on its slot's stream, inside its arena
     block: [model workspace | grid | P | dP | d_obs | sig_obs | out].  A request
-    with method "modit" takes the MODIT cross-section (n_gamma width nodes)."""
+    with method "modit" takes the MODIT cross-section (n_gamma width nodes).
+    With hi_streams (one higher-priority stream per slot), line-sum requests of
+    fewer than hi_evals Voigt evaluations run on their slot's high-priority stream,
+    so that the block scheduler runs their kernels ahead of the long ones."""
 
-    def __init__(self, pool: LinePool, arena_tensor, streams, prec=1, fail_hook=None, n_gamma=16):
+    def __init__(self, pool: LinePool, arena_tensor, streams, prec=1, fail_hook=None, n_gamma=16, hi_streams=None,
+                 hi_evals=1e11):
         import torch
         from . import xs
         self.torch, self.xs = torch, xs
@@ -275,6 +280,7 @@ class LibxsExecutor:
         self.arena_t = arena_tensor
         self.base = arena_tensor.data_ptr()
         self.streams = streams
+        self.hi_streams, self.hi_evals = hi_streams, float(hi_evals)
         self.prec = prec
         self.fail_hook = fail_hook
         self.n_gamma = int(n_gamma)
@@ -354,7 +360,9 @@ class LibxsExecutor:
         lay, _ = self._layout(r)
         off0 = block[0]
         ptr = {k: self.base + off0 + o for k, (o, n) in lay.items()}
-        st = self.streams[slot]
+        short = self.hi_streams is not None and r.method == "lpf" and self.work(r) < self.hi_evals
+        st = self.hi_streams[slot] if short else self.streams[slot]
+        r.high_priority = short
         # request inputs from the host (pinned), copied on the slot's stream
         N, L = r.n_grid, r.n_layers
         nu = W.grid_lognu(N)
@@ -383,10 +391,13 @@ class LibxsExecutor:
             out_h.copy_(self.arena_t.narrow(0, off0 + lay["out"][0], 48).view(torch.float64), non_blocking=True)
             ev = torch.cuda.Event()
             ev.record(st)
-        # Voigt evaluations of the line sum (forward and adjoint); MODIT evaluates none
-        r.evals = 0 if r.method == "modit" else \
-            2 * L * (self.pool.cut_fraction(self.pool.nearest(r.n_lines)) * N + self.pool.co_fraction * N)
+        r.evals = 0 if r.method == "modit" else self.work(r)  # MODIT evaluates no Voigt profile
         return (ev, out_h, host)
+
+    def work(self, r):
+        """Voigt evaluations of the request's line sum, forward and adjoint."""
+        N = r.n_grid
+        return 2 * r.n_layers * (self.pool.cut_fraction(self.pool.nearest(r.n_lines)) * N + self.pool.co_fraction * N)
 
     def ready(self, r):
         return r.handle[0].query()
@@ -510,10 +521,15 @@ def summarize(finished, wall_s):
             "mean_s": float(np.mean(lat)), "wall_s": wall_s}
 
 
-def make_server(arena_bytes=int(40e9), slots=4, prec=1, device="cuda", fail_hook=None, pool=None, n_gamma=16):
+def make_server(arena_bytes=int(40e9), slots=4, prec=1, device="cuda", fail_hook=None, pool=None, n_gamma=16,
+                priority=False, hi_evals=1e11):
+    """Scheduler + LibxsExecutor over one arena; with priority, short line-sum
+    requests (< hi_evals evaluations) run on high-priority streams."""
     import torch
     pool = pool or LinePool(device)
     arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=device)
     streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
-    ex = LibxsExecutor(pool, arena, streams, prec=prec, fail_hook=fail_hook, n_gamma=n_gamma)
+    hi = [torch.cuda.Stream(device=device, priority=-1) for _ in range(slots)] if priority else None
+    ex = LibxsExecutor(pool, arena, streams, prec=prec, fail_hook=fail_hook, n_gamma=n_gamma, hi_streams=hi,
+                       hi_evals=hi_evals)
     return Scheduler(ex, int(arena_bytes), slots), pool

@@ -48,6 +48,23 @@ def test_same_alone_and_in_the_mix(pool):
         np.testing.assert_array_equal(r.result, alone[r.rid])  # deterministic reductions: bit-identical
 
 
+def test_priority_streams_change_no_result(pool):
+    """With short requests on high-priority streams the results are those of the
+    server without priorities, bit for bit."""
+    from paper_2105_14782_gb300 import serve
+    base, prio = _requests(12), _requests(12)
+    for reqs, flag in ((base, False), (prio, True)):
+        s, _ = serve.make_server(arena_bytes=2 << 30, slots=4, pool=pool, priority=flag, hi_evals=1e9)
+        for r in reqs:
+            s.submit(r)
+        s.drain(timeout_s=120)
+    assert not any(r.high_priority for r in base)
+    assert any(r.high_priority for r in prio) and not all(r.high_priority for r in prio)
+    for a, b in zip(base, prio):
+        assert a.status == b.status == serve.DONE
+        np.testing.assert_array_equal(a.result, b.result)
+
+
 def test_matches_direct_model_call(pool):
     from paper_2105_14782_gb300 import serve, xs
     r = _requests(3)[2]
